@@ -1,0 +1,377 @@
+"""Benchmark of the CRSH path on GB300: secondary rays per second for one frame.
+
+A step is one pass of the whole path over one frame's primary-hit buffer:
+crsh_hash_sort -> crsh_build -> crsh_traverse -> crsh_closest_hit.  Default
+workload: 512x512, 60,162 triangles in 17 meshes (30 % mirror, 20 % glass),
+2 lights, B = 16, L = 4 (all inputs synthetic, seeded).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 the script runs under torchrun: every rank runs its own replica of
+the frame (the path has no exchange step), ranks meet at a barrier around the
+timed steps and the slowest rank's time counts (weak scaling).
+--impl reference times the CPU oracle (the plain restatement of the method
+used by the tests) on the host cores instead; under torchrun only rank 0 runs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "secondary Mrays/s, batched vs plain at exact hits; tri tests/ray; adjoint ms"
+UNIT = "Mrays/s"
+MT_FLOPS = 46          # FP32 operations of one Moller-Trumbore test
+EQ9_FLOPS = 27         # FP32 operations of one sphere-cone test (eq. 9)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def reduce_over_ranks(local_ms: float, local_units: float, world: int):
+    """Max time and total units over ranks (identity when world == 1)."""
+    if world <= 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda") if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def workload_description(w):
+    return (f"plain CRSH frame: {w.width}x{w.height} primary hits, {w.scene.n_tris:,} triangles in "
+            f"{w.scene.n_meshes} meshes, {w.lights.shape[0]} lights, shadow+reflection+refraction rays, "
+            f"B={w.bundle}, L={w.levels}")
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def crop_gbuffer(w, side: int):
+    """Central side x side crop of the frame's G-buffer (same scene, same ray mix)."""
+    W, H = w.width, w.height
+    x0, y0 = (W - side) // 2, (H - side) // 2
+    idx = (np.arange(y0, y0 + side)[:, None] * W + np.arange(x0, x0 + side)[None, :]).reshape(-1)
+    return {k: np.ascontiguousarray(v[idx]) for k, v in w.gbuffer.items()}
+
+
+def oracle_step(w, g):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.run_crsh(g, w.lights, w.shadow_cull, w.hash_lo, w.hash_hi, w.scene, w.bundle, w.levels,
+                        w.build_pads())
+    return time.perf_counter() - t0, r["counters"]["rays"]
+
+
+def cpu_baseline(w, budget_s: float = 15.0, side: int = 128):
+    """Oracle over central crops, growing until one pass costs ~budget_s / 3."""
+    import oracle
+    oracle.compile_native()
+    g = crop_gbuffer(w, side)
+    dt, n = oracle_step(w, g)
+    while dt < budget_s / 6 and side * 2 <= min(w.width, w.height):
+        side *= 2
+        g = crop_gbuffer(w, side)
+        dt, n = oracle_step(w, g)
+    reps, tot_t, tot_n = 1, dt, n
+    while tot_t < budget_s * 0.5:
+        dt, n = oracle_step(w, g)
+        tot_t += dt
+        tot_n += n
+        reps += 1
+    return {"value": tot_n / tot_t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"central {side}x{side} crop of the frame ({n} rays), {reps} pass(es), single-threaded C"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.compile_native()
+    side = args.ref_crop
+    g = crop_gbuffer(w, side)
+    for _ in range(args.warmup):
+        oracle_step(w, g)
+    times, rays = [], 0
+    for _ in range(args.steps):
+        dt, n = oracle_step(w, g)
+        times.append(dt)
+        rays += n
+    tot = sum(times)
+    value = rays / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_description(w), "sample": f"central {side}x{side} crop per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"central {side}x{side} crop of the frame ({rays // args.steps} rays) "
+                                       f"per step, single-threaded C"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def launches_per_step(levels: int, compress: bool) -> int:
+    """Kernels of libcrsh.so launched by one pass (count of <<<>>> in the call sequence)."""
+    hash_sort = 5 + 1 + (1 if compress else 0) + 2 + 4 + (1 if compress else 0) + 1   # tables, gen, chunk, hist+plan, 4 passes, pos, gather
+    build = levels
+    traverse = 3 + 2 * (levels - 1) + 1
+    closest = 3
+    return hash_sort + build + traverse + closest
+
+
+def run_gpu(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2312_06538_gb300 import pipeline as pl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+
+    p = pl.workload_pipeline(w, device=dev)
+    hp, bp = pl.workload_params(w)
+    g_host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+              pl.Pipeline.gbuffer_to_device(w.gbuffer, "cpu").items()}
+    g_dev = {k: v.to(dev) for k, v in g_host.items()}
+    lights = torch.from_numpy(w.lights).to(dev)
+    gstruct = p.gbuffer_struct(g_dev)
+    c = p.run_fit(gstruct, lights, hp, bp)          # sizes the pair lists, checks the status
+    n_rays = c["rays"]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    def step(ev):
+        ev[0].record(stream)
+        p.hash_sort(gstruct, lights, hp, sh)
+        ev[1].record(stream)
+        p.build(bp, sh)
+        ev[2].record(stream)
+        p.traverse(True, sh)
+        ev[3].record(stream)
+        p.closest_hit(sh)
+        ev[4].record(stream)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    warm = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step(warm)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(props.index if hasattr(props, "index") else local) as clk:
+        torch.cuda.synchronize(dev)
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)       # L2 (129 MB) flushed between timed steps, outside the events
+            step(evs[k])
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall0
+        if world > 1:
+            dist.barrier()
+    stage = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(args.steps)])
+    step_ms = stage.sum(1)
+    local_ms = float(step_ms.sum())
+    c_after = p.read_counters()
+    assert c_after["status"] == 0 and c_after["rays"] == n_rays
+    tot_ms, tot_units = reduce_over_ranks(local_ms, float(n_rays) * args.steps, world)
+    value = tot_units / (tot_ms * 1e-3) / 1e6
+
+    # end to end through the API with host buffers: pinned G-buffer in, hits out
+    hits_host = {k: torch.empty(p.ray_capacity, dtype=t.dtype).pin_memory()
+                 for k, t in (("tri", p.hit_tri), ("t", p.hit_t), ("u", p.hit_u), ("v", p.hit_v))}
+    n_host = torch.empty(1, dtype=torch.int32).pin_memory()
+    h2d = sum(int(v.numel() * v.element_size()) for v in g_host.values()) + int(lights.numel() * 4)
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for kk, v in g_host.items():
+            g_dev[kk].copy_(v, non_blocking=True)
+        p.run(gstruct, lights, hp, bp, stream=sh)
+        n_host.copy_(p.n_rays, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        n = int(n_host.item())
+        for kk, src in (("tri", p.hit_tri), ("t", p.hit_t), ("u", p.hit_u), ("v", p.hit_v)):
+            hits_host[kk][:n].copy_(src[:n], non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if k >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    d2h = 4 + 16 * n_rays
+    e2e_local_ms = 1e3 * sum(e2e_times)
+    e2e_ms, e2e_units = reduce_over_ranks(e2e_local_ms, float(n_rays) * args.steps, world)
+    e2e_value = e2e_units / (e2e_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (final tests): achieved FP32 flops per launch / event time
+    peaks, peak_src = _peaks()
+    clocks = clk.summary()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tf = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    ch_ms = float(stage[:, 3].mean())
+    achieved = c["final_tests"] * MT_FLOPS / (ch_ms * 1e-3) / 1e12
+    tr_ms = float(stage[:, 2].mean())
+    eq9_tests = sum(c["tests"]) + c["mesh_tests"]
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            traffic = json.load(open(tp)).get("k_closest_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"kernel": "crsh_closest_hit (k_closest + fill + finalize)", "bound": "alu",
+                "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
+                "traffic": traffic,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                               f"(max SM clock, {peak_src} peaks file)",
+                "algorithmic": f"{MT_FLOPS} FP32 flops per ray-triangle test x {c['final_tests']} tests per launch"}
+    total_tests = c["final_tests"] + eq9_tests
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene, software-rasterised G-buffer)",
+        "config": {"workload": workload_description(w), "pixels": w.n_pixels, "triangles": w.scene.n_tris,
+                   "rays_per_step": n_rays, "bundle": w.bundle, "levels": w.levels,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed between timed steps (512 MiB write outside the step events)"},
+        "tri_tests_per_ray": c["final_tests"] / max(1, n_rays),
+        "all_tests_per_ray": total_tests / max(1, n_rays),
+        "bruteforce_tests_per_ray": w.scene.n_tris,
+        "stage_ms": {"hash_sort": float(stage[:, 0].mean()), "build": float(stage[:, 1].mean()),
+                     "traverse": tr_ms, "closest_hit": ch_ms},
+        "traverse_eq9_tflops": eq9_tests * EQ9_FLOPS / (tr_ms * 1e-3) / 1e12,
+        "wall_ms_timed_region": 1e3 * t_wall,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step(w.levels, True) * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--res", type=int, default=None)
+    ap.add_argument("--ref-crop", type=int, default=128)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
+    import synthetic
+    w = synthetic.make(args.config, res=args.res)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

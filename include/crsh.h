@@ -1,0 +1,263 @@
+/* crsh.h - C ABI of the Coherent Ray-Space Hierarchy library for NVIDIA GB300
+ * (sm_103a).
+ *
+ * Method: Reis, Costa, Pereira, "Ray-Tracing With a Coherent Ray-Space
+ * Hierarchy" (arXiv 2312.06538).  The calls follow the paper's pipeline:
+ *
+ *   crsh_prepare_scene   triangle bounding spheres and Moller-Trumbore layout
+ *   crsh_hash_sort       Section 3.3.2-3.3.5: secondary ray generation from the
+ *                        primary-hit buffer, per-type hashing, trimming,
+ *                        compression, radix sort, decompression
+ *   crsh_build           Section 3.3.6, eqs. 1-8: bottom-up sphere-cone levels
+ *   crsh_traverse        Section 3.3.7, eq. 9: whole-mesh then triangle culling,
+ *                        top-down, into compacted (node, triangle) pair lists
+ *   crsh_closest_hit     Section 3.3.8: final Moller-Trumbore tests, closest hit
+ *   crsh_closest_hit_backward   gradients of the closest hit (not in the paper)
+ *
+ * Conventions shared by every call
+ *  - Pointers inside the structs are DEVICE pointers unless a field says
+ *    otherwise; the structs themselves live in host memory and are read during
+ *    the call only.
+ *  - The caller owns every buffer (inputs, outputs, workspaces).  The library
+ *    allocates no device memory.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream).  Data-dependent sizes (ray count, pair counts) stay on
+ *    the device; no call synchronises with the host, so the sequence can be
+ *    captured in a CUDA graph.
+ *  - Argument errors are returned synchronously and nothing is launched.
+ *    Errors found on the device (capacity exceeded, a wait that timed out)
+ *    are recorded in crsh_counters.status (first error wins) and in the
+ *    *_needed fields; read them after synchronising.  Results are then
+ *    incomplete but every kernel still terminates.
+ *  - Results are deterministic: identical inputs give identical bits.
+ *  - Ray directions are expected to be finite and non-zero; t is measured in
+ *    units of the stored direction vector.
+ */
+#ifndef CRSH_H
+#define CRSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int crsh_status;
+#define CRSH_OK                  0
+#define CRSH_ERR_INVALID_ARG     1  /* bad pointer, size or parameter (synchronous) */
+#define CRSH_ERR_CAPACITY        2  /* an output or workspace was too small (device) */
+#define CRSH_ERR_CUDA            3  /* a CUDA runtime call failed (synchronous) */
+#define CRSH_ERR_TIMEOUT         4  /* a bounded device-side wait gave up (device) */
+#define CRSH_ERR_NOT_IMPLEMENTED 5
+#define CRSH_ERR_BAD_INPUT       6  /* input data the method cannot use (device) */
+
+#define CRSH_MAX_LEVELS 8
+
+#define CRSH_RAY_SHADOW     0
+#define CRSH_RAY_REFLECTION 1
+#define CRSH_RAY_REFRACTION 2
+
+#define CRSH_MAT_DIFFUSE 0
+#define CRSH_MAT_MIRROR  1
+#define CRSH_MAT_GLASS   2
+
+/* Primary-hit buffer (Section 3.2: the rasterised G-buffer of position,
+ * normal and material that secondary rays start from), one entry per pixel,
+ * structure of arrays. */
+typedef struct {
+    const float *px, *py, *pz;   /* hit position */
+    const float *nx, *ny, *nz;   /* unit surface normal facing the viewer */
+    const float *ix, *iy, *iz;   /* unit incident (camera ray) direction */
+    const uint32_t *material;    /* CRSH_MAT_*; mirror: reflection ray, glass: reflection + refraction */
+    const uint8_t *hit;          /* 1 if the pixel saw geometry */
+    uint32_t n_pixels;
+} crsh_gbuffer;
+
+/* Rays given directly instead of a G-buffer (hashed and sorted as they are). */
+typedef struct {
+    const float *ox, *oy, *oz, *dx, *dy, *dz, *tmax;
+    const uint8_t *type;         /* CRSH_RAY_* */
+    const uint8_t *light;        /* light index of shadow rays (ignored otherwise) */
+    uint32_t n;
+} crsh_rays_in;
+
+/* Hash and sort parameters (Section 3.3.2, Figures 2-3).  Key layout, 32 bits:
+ *   [31:30] ray type
+ *   shadow:      [29 : tb+pb] light index, [tb+pb-1 : 0] direction code
+ *   refl./refr.: [29 : tb+pb] Morton code of the origin cell (cell_bits per
+ *                axis over the box lo..hi), [tb+pb-1 : 0] direction code
+ * The direction code is the Z-order interleave (phi bit first) of the
+ * theta = acos(dz) bin (tb bits) and the phi = atan2(dy, dx) bin (pb bits);
+ * bins are decided by comparison with FP32 tables of cos(k pi / 2^tb) and
+ * tan(j pi / 2^pb), so every implementation gets the same keys. */
+typedef struct {
+    float lo[3], hi[3];            /* box of secondary-ray origins quantised into cells */
+    uint32_t shadow_theta_bits;    /* default 13 */
+    uint32_t shadow_phi_bits;      /* default 13; >= 3; light bits = 30 - theta - phi */
+    uint32_t sec_cell_bits;        /* default 5 (per axis) */
+    uint32_t sec_theta_bits;       /* default 7 */
+    uint32_t sec_phi_bits;         /* default 8; 3*cell + theta + phi <= 30 */
+    uint32_t shadow_cull;          /* 1: shadow ray only if n.(P - L) < 0 (light in front) */
+    uint32_t sort;                 /* 0: keep generation order (the unsorted-RSH comparison mode) */
+    uint32_t compress;             /* 1: compress equal-key runs into chunks before sorting */
+} crsh_hash_params;
+
+/* Sorted rays (output of crsh_hash_sort, input of every later call). */
+typedef struct {
+    float *ox, *oy, *oz, *dx, *dy, *dz, *tmax;
+    uint8_t *type;                 /* CRSH_RAY_* */
+    uint32_t *ray_id;              /* generation-order index of each sorted ray */
+    uint32_t *pixel;               /* pixel (G-buffer input) or input index of each sorted ray */
+    uint32_t capacity;             /* entries allocated in every array above */
+} crsh_rays;
+
+/* Counters in the schema of the paper's Tables 1-3, plus the device status.
+ * Device memory, written by the calls. */
+typedef struct {
+    unsigned long long rays;       /* secondary rays after trimming */
+    unsigned long long chunks;     /* chunks after compression (Section 3.3.3) */
+    unsigned long long mesh_tests; /* top nodes x whole-mesh spheres tested */
+    unsigned long long mesh_hits;
+    unsigned long long tests[CRSH_MAX_LEVELS];        /* sphere-cone tests made, index l-1 = level l */
+    unsigned long long hits[CRSH_MAX_LEVELS];         /* accepted (node, triangle) pairs */
+    unsigned long long tests_paper[CRSH_MAX_LEVELS];  /* B per parent pair (the tables' convention) */
+    unsigned long long final_tests;                   /* ray-triangle tests made */
+    unsigned long long final_tests_paper;             /* B per level-1 pair */
+    unsigned long long final_hits;                    /* ray-triangle tests that hit */
+    unsigned long long needed_pairs;                  /* largest pair list any level produced */
+    unsigned int status;                              /* first device-side crsh_status, 0 = OK */
+    unsigned int reserved;
+} crsh_counters;
+
+/* Triangle meshes.  Meshes are contiguous triangle ranges. */
+typedef struct {
+    const float *v0x, *v0y, *v0z, *v1x, *v1y, *v1z, *v2x, *v2y, *v2z;
+    uint32_t n_tris;
+    const uint32_t *mesh_first_tri;  /* n_meshes + 1 entries; mesh m = [first[m], first[m+1]) */
+    const float *mesh_sphere;        /* 4 floats per mesh: centre xyz, radius (encloses the mesh) */
+    uint32_t n_meshes;
+    float *tri_sphere;               /* 4 floats per triangle, written by crsh_prepare_scene */
+    float *tri_mt;                   /* 12 floats per triangle, written by crsh_prepare_scene */
+} crsh_scene;
+
+typedef struct {
+    uint32_t bundle;                 /* B: children per node, power of two in [2, 32] */
+    uint32_t levels;                 /* L: levels built and traversed, 1..CRSH_MAX_LEVELS */
+    float sphere_pad_rel, sphere_pad_abs;  /* radius -> r (1 + rel) + abs after each node */
+    float cone_pad_rel, cone_pad_abs;      /* spread -> s (1 + rel) + abs (radians) */
+} crsh_build_params;
+
+/* Levels of sphere-cone nodes (Section 3.3.6: 8 floats per node). */
+typedef struct {
+    float *sphere[CRSH_MAX_LEVELS];  /* 4 floats per node: centre xyz, radius */
+    float *cone[CRSH_MAX_LEVELS];    /* 4 floats per node: unit axis xyz, spread (half-angle) */
+    float *trig[CRSH_MAX_LEVELS];    /* 2 floats per node: tan(spread), 1/cos(spread), for eq. 9 */
+    uint32_t capacity[CRSH_MAX_LEVELS]; /* nodes allocated per level: >= ceil(rays / B^l) */
+    uint32_t *count;                 /* device, CRSH_MAX_LEVELS entries: nodes per level */
+    uint32_t levels, bundle;
+} crsh_hierarchy;
+
+typedef struct {
+    uint32_t mesh_cull;              /* 1: whole-mesh spheres at the top level (Section 3.3.7) */
+} crsh_traverse_params;
+
+/* Level-1 (node, triangle) pairs grouped by node, triangles ascending. */
+typedef struct {
+    uint32_t *node, *tri;            /* capacity entries each */
+    uint32_t *node_offsets;          /* level-1 node count + 1 entries: CSR over nodes */
+    uint32_t *count;                 /* device: pairs written */
+    uint64_t capacity;
+} crsh_pairs;
+
+/* Closest hits in generation order (ray_id). tri = -1: no hit (t = u = v = 0). */
+typedef struct {
+    int32_t *tri;
+    float *t, *u, *v;
+} crsh_hits;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int crsh_version(void);
+const char *crsh_status_string(crsh_status s);
+
+/* Triangle bounding spheres (centroid centre, largest vertex distance, padded
+ * outward for FP32 rounding) and the (v0, v1 - v0, v2 - v0) layout used by the
+ * final tests.  Writes scene->tri_sphere and scene->tri_mt. */
+crsh_status crsh_prepare_scene(const crsh_scene *scene, void *stream);
+
+/* Workspace bytes crsh_hash_sort needs for up to `capacity` rays generated
+ * from at most `max_pixels` G-buffer pixels (0 for crsh_rays_in input). */
+size_t crsh_hash_sort_workspace(uint32_t capacity, uint32_t max_pixels);
+
+/* Section 3.3.2-3.3.5.  Exactly one of `gbuffer` and `rays_in` is non-NULL.
+ * From a G-buffer: for every hit pixel one shadow ray per light (origin at the
+ * light, direction to the hit point, t_max = 0.9999 of the distance), a
+ * reflection ray for mirror and glass, and a refraction ray for glass (IOR
+ * 1.5, none on total internal reflection); empty slots are trimmed, keeping
+ * pixel-major order.  Every ray gets its per-type key; rays are then sorted
+ * by key, equal keys keeping generation order (optionally through chunk
+ * compression, which gives the same order).
+ * lights: device, 3 floats per light (n_lights <= 2^(30 - tb - pb)).
+ * Outputs: `out` sorted rays, `keys_out` sorted keys (device, capacity
+ * entries), `n_out` device ray count, counters->rays/chunks (the call resets
+ * the whole counters struct first).  More rays than out->capacity:
+ * CRSH_ERR_CAPACITY on the device, first capacity rays kept in order. */
+crsh_status crsh_hash_sort(const crsh_gbuffer *gbuffer, const crsh_rays_in *rays_in,
+                           const float *lights, uint32_t n_lights, const crsh_hash_params *params,
+                           crsh_rays *out, uint32_t *keys_out, uint32_t *n_out,
+                           crsh_counters *counters, void *workspace, size_t workspace_bytes,
+                           void *stream);
+
+/* Section 3.3.6.  Level-1 node j bounds sorted rays [jB, min(jB + B, n));
+ * level-l node j bounds level-(l-1) nodes [jB, ...).  Cones: eqs. 1-4 fold
+ * the rays of a level-1 node in order; eqs. 5-6 merge child cones; spheres:
+ * eqs. 7-8; children merge as a balanced binary tree in child order.  Nodes
+ * are padded outward (params) so the FP32 hierarchy contains its rays.
+ * n_rays: device count from crsh_hash_sort.  Writes out->sphere/cone/trig for
+ * levels 1..params->levels and out->count; sets out->levels/bundle. */
+crsh_status crsh_build(const crsh_rays *rays, const uint32_t *n_rays, const crsh_build_params *params,
+                       crsh_hierarchy *out, void *stream);
+
+/* Workspace bytes crsh_traverse needs for pair lists of `pair_capacity`
+ * entries per level over hierarchy `h` and `n_tris` triangles. */
+size_t crsh_traverse_workspace(const crsh_hierarchy *h, uint32_t n_tris, uint32_t n_meshes,
+                               uint64_t pair_capacity);
+
+/* Section 3.3.7, eq. 9.  Top level: each top node against each whole-mesh
+ * sphere (all meshes when mesh_cull = 0), then against the triangle spheres of
+ * the meshes it meets; levels L-1 .. 1: each pair (p, t) of the level above
+ * expands to the children of p, each tested against t.  Every level's list is
+ * compacted in order.  Output: level-1 pairs grouped by node (out), counters
+ * tests, hits, tests_paper, mesh_tests, mesh_hits and needed_pairs (reset by this call).  A list
+ * longer than out->capacity sets CRSH_ERR_CAPACITY and needed_pairs. */
+crsh_status crsh_traverse(const crsh_hierarchy *h, const crsh_scene *scene,
+                          const crsh_traverse_params *params, crsh_pairs *out,
+                          crsh_counters *counters, void *workspace, size_t workspace_bytes,
+                          void *stream);
+
+/* Workspace bytes crsh_closest_hit / crsh_bruteforce_closest_hit need. */
+size_t crsh_closest_hit_workspace(uint32_t ray_capacity);
+
+/* Section 3.3.8.  For every level-1 pair (n, t) and every ray of n:
+ * Moller-Trumbore in FP32 (two-sided, inclusive edges, 0 < t <= t_max); the
+ * closest hit per ray is the smallest (t, triangle id).  The (t, u, v) of the
+ * winning triangle are then recomputed in FP64 from the FP32 inputs and
+ * rounded to FP32.  Hits are written at each ray's ray_id.  Counters final_*
+ * reset and written by this call.  Workspace: crsh_closest_hit_workspace. */
+crsh_status crsh_closest_hit(const crsh_hierarchy *h, const crsh_rays *rays, const uint32_t *n_rays,
+                             const crsh_scene *scene, const crsh_pairs *pairs, crsh_hits *out,
+                             crsh_counters *counters, void *workspace, size_t workspace_bytes,
+                             void *stream);
+
+/* Every ray against every triangle with the same test (Section 1's N x M
+ * baseline); results bit-identical to crsh_closest_hit when culling is
+ * conservative. */
+crsh_status crsh_bruteforce_closest_hit(const crsh_rays *rays, const uint32_t *n_rays,
+                                        const crsh_scene *scene, crsh_hits *out, void *workspace,
+                                        size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRSH_H */

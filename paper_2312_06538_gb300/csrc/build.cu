@@ -1,0 +1,260 @@
+// Section 3.3.6: bottom-up hierarchy of sphere-cones, and the per-triangle
+// data the traversal and final tests read (triangle bounding spheres,
+// Moller-Trumbore edge layout).
+//
+// GB300 design: one thread per node.  Level-1 nodes read their B sorted rays
+// (consecutive, so a warp's loads cover one contiguous stretch of each SoA
+// array and stay in L1), fold the cone ray by ray (eqs. 1-4) and merge the
+// spheres (eqs. 7-8) as a balanced binary tree evaluated with a binary-counter
+// stack of log2(B) + 1 entries.  Upper levels merge B children the same way
+// (eqs. 5-8).  Every node is padded outward after its merge so the FP32
+// hierarchy contains its rays, and stores tan(spread), 1/cos(spread) for the
+// eq. 9 tests of the traversal.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace crsh {
+
+struct SC {
+    f3 c;
+    float r;
+    f3 x;
+    float phi;
+};
+
+// eqs. 7-8: sphere union, centre at the midpoint.
+__device__ __forceinline__ void sphere_union(SC& a, const SC& b) {
+    f3 c = (a.c + b.c) * 0.5f;
+    float r = 0.5f * len(b.c - a.c) + fmaxf(a.r, b.r);
+    a.c = c;
+    a.r = r;
+}
+
+// eqs. 5-6: cone union about the normalised axis sum; spread = half the axis
+// angle + the larger child spread; opposite axes give the whole sphere.
+__device__ __forceinline__ void cone_union(SC& a, const SC& b) {
+    f3 s = a.x + b.x;
+    float ls = len(s);
+    if (a.phi >= PI_F || b.phi >= PI_F || !(ls > 1e-6f)) {
+        a.phi = PI_F;
+        return;
+    }
+    float th = angle(a.x, b.x);
+    a.x = s * (1.0f / ls);
+    a.phi = fminf(PI_F, 0.5f * th + fmaxf(a.phi, b.phi));
+}
+
+// eqs. 1-4: widen (x, phi) to hold direction r: far edge e of the current cone
+// (eq. 2, with q the unit normal to x in the plane of x and r pointing away
+// from r, eq. 1), new axis the bisector of e and r (eq. 3), new spread the
+// angle between axis and r (eq. 4).  When the result would be a cone of
+// half-angle >= pi/2 (theta + phi >= pi), the node takes the whole sphere,
+// which eq. 9 accepts everywhere anyway.
+__device__ __forceinline__ void cone_add_ray(f3& x, float& phi, f3 r) {
+    if (phi >= PI_F) return;
+    float th = angle(x, r);
+    if (th <= phi) return;
+    if (th + phi >= PI_F - 1e-6f) {
+        phi = PI_F;
+        return;
+    }
+    f3 q = cross(cross(r, x), x);
+    float lq = len(q);
+    if (!(lq > 0.0f)) {   // r numerically parallel to x: nothing to widen
+        phi = fmaxf(phi, th);
+        return;
+    }
+    q = q * (1.0f / lq);
+    float sp, cp;
+    sincosf(phi, &sp, &cp);
+    f3 e = x * cp + q * sp;
+    x = unit(e + r);
+    phi = angle(x, r);
+}
+
+struct Pads {
+    float sr, sa, cr, ca;
+};
+
+// Caller's padding, plus a margin of a few FP32 ulps of the centre's
+// coordinates that covers the rounding of the eq. 9 test near this node.
+__device__ __forceinline__ void pad_node(SC& n, const Pads& p) {
+    n.r = n.r * (1.0f + p.sr) + p.sa + 3.9e-6f * (fabsf(n.c.x) + fabsf(n.c.y) + fabsf(n.c.z));
+    n.phi = fminf(PI_F, n.phi * (1.0f + p.cr) + p.ca);
+}
+
+// Balanced binary tree of merges in item order, evaluated as a binary counter:
+// equal-size neighbours on the stack merge (left operand = earlier items); at
+// the end the stack folds from the top.  Identical to merging item i with
+// item i + s at steps s = 1, 2, 4, ... whenever i + s exists.
+template <bool CONES>
+struct TreeMerge {
+    SC st[7];
+    unsigned sz[7];
+    int top = 0;
+    __device__ __forceinline__ void merge_top() {
+        sphere_union(st[top - 2], st[top - 1]);
+        if (CONES) cone_union(st[top - 2], st[top - 1]);
+        sz[top - 2] += sz[top - 1];
+        --top;
+    }
+    __device__ __forceinline__ void push(const SC& v) {
+        st[top] = v;
+        sz[top] = 1;
+        ++top;
+        while (top >= 2 && sz[top - 1] == sz[top - 2]) merge_top();
+    }
+    __device__ __forceinline__ SC finish() {
+        while (top > 1) merge_top();
+        return st[0];
+    }
+};
+
+struct LevelOut {
+    float4* sphere;
+    float4* cone;
+    float2* trig;
+    unsigned cap;
+};
+
+__device__ __forceinline__ void store_node(const LevelOut& o, unsigned j, const SC& n) {
+    o.sphere[j] = make_float4(n.c.x, n.c.y, n.c.z, n.r);
+    o.cone[j] = make_float4(n.x.x, n.x.y, n.x.z, n.phi);
+    float t, s;
+    if (n.phi >= 0.5f * PI_F - 1e-6f) {
+        t = s = __int_as_float(0x7f800000);   // accept everything (eq. 9 reading)
+    } else {
+        float sp, cp;
+        sincosf(n.phi, &sp, &cp);
+        t = sp / cp;
+        s = 1.0f / cp;
+        // round both up by a few ulps so the FP32 test stays conservative
+        t = t * (1.0f + 4.8e-7f);
+        s = s * (1.0f + 4.8e-7f);
+    }
+    o.trig[j] = make_float2(t, s);
+}
+
+struct RaysIn {
+    const float *ox, *oy, *oz, *dx, *dy, *dz;
+};
+
+struct Caps {
+    unsigned v[CRSH_MAX_LEVELS];
+};
+
+__global__ void k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned B, unsigned L, Pads pads, LevelOut out,
+                           unsigned* counts, Caps caps) {
+    const unsigned n = *n_ptr;
+    const unsigned cnt = (n + B - 1) / B;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned c = n;
+        for (unsigned l = 0; l < CRSH_MAX_LEVELS; ++l) {
+            if (l < L) {
+                c = (c + B - 1) / B;
+                c = min(c, caps.v[l]);   // capacities are checked on the host
+                counts[l] = c;
+            } else {
+                counts[l] = 0;
+            }
+        }
+    }
+    const unsigned lim = min(cnt, out.cap);
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < lim; j += gridDim.x * blockDim.x) {
+        const unsigned first = j * B, last = min(first + B, n);
+        f3 x = unit(mk3(rays.dx[first], rays.dy[first], rays.dz[first]));
+        float phi = 0.0f;
+        TreeMerge<false> tm;
+        for (unsigned i = first; i < last; ++i) {
+            if (i > first) cone_add_ray(x, phi, unit(mk3(rays.dx[i], rays.dy[i], rays.dz[i])));
+            SC leaf;
+            leaf.c = mk3(rays.ox[i], rays.oy[i], rays.oz[i]);
+            leaf.r = 0.0f;
+            tm.push(leaf);
+        }
+        SC nd = tm.finish();
+        nd.x = x;
+        nd.phi = phi;
+        pad_node(nd, pads);
+        store_node(out, j, nd);
+    }
+}
+
+__global__ void k_build_up(const float4* csph, const float4* ccone, const unsigned* counts, unsigned level_idx,
+                           unsigned B, Pads pads, LevelOut out) {
+    const unsigned below = counts[level_idx - 1];
+    const unsigned cnt = counts[level_idx];
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += gridDim.x * blockDim.x) {
+        const unsigned first = j * B, last = min(first + B, below);
+        TreeMerge<true> tm;
+        for (unsigned i = first; i < last; ++i) {
+            float4 s = csph[i], c = ccone[i];
+            SC ch;
+            ch.c = mk3(s.x, s.y, s.z);
+            ch.r = s.w;
+            ch.x = mk3(c.x, c.y, c.z);
+            ch.phi = c.w;
+            tm.push(ch);
+        }
+        SC nd = tm.finish();
+        pad_node(nd, pads);
+        store_node(out, j, nd);
+    }
+}
+
+crsh_status build_launch(const crsh_rays* rays, const uint32_t* n_rays, const crsh_build_params* bp,
+                         crsh_hierarchy* h, cudaStream_t s, const DeviceInfo& dev) {
+    const unsigned B = bp->bundle, L = bp->levels;
+    Pads pads{bp->sphere_pad_rel, bp->sphere_pad_abs, bp->cone_pad_rel, bp->cone_pad_abs};
+    h->levels = L;
+    h->bundle = B;
+    Caps caps{};
+    for (unsigned l = 0; l < L; ++l) caps.v[l] = h->capacity[l];
+    RaysIn ri{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz};
+    LevelOut o1{reinterpret_cast<float4*>(h->sphere[0]), reinterpret_cast<float4*>(h->cone[0]),
+                reinterpret_cast<float2*>(h->trig[0]), h->capacity[0]};
+    const unsigned blocks1 = (h->capacity[0] + 127) / 128;
+    const unsigned grid1 = blocks1 < (unsigned)dev.sms * 16 ? (blocks1 ? blocks1 : 1) : dev.sms * 16;
+    k_build_l1<<<grid1, 128, 0, s>>>(ri, n_rays, B, L, pads, o1, h->count, caps);
+    for (unsigned l = 1; l < L; ++l) {
+        LevelOut o{reinterpret_cast<float4*>(h->sphere[l]), reinterpret_cast<float4*>(h->cone[l]),
+                   reinterpret_cast<float2*>(h->trig[l]), h->capacity[l]};
+        const unsigned blocks = (h->capacity[l] + 127) / 128;
+        const unsigned grid = blocks < (unsigned)dev.sms * 16 ? (blocks ? blocks : 1) : dev.sms * 16;
+        k_build_up<<<grid, 128, 0, s>>>(reinterpret_cast<const float4*>(h->sphere[l - 1]),
+                                        reinterpret_cast<const float4*>(h->cone[l - 1]), h->count, l, B, pads, o);
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Scene preparation: triangle spheres (centroid, largest vertex distance,
+// padded outward by a few FP32 ulps of the coordinates) and the
+// (v0, v1 - v0, v2 - v0) layout read by the final tests.
+// ---------------------------------------------------------------------------
+__global__ void k_prepare(crsh_scene sc) {
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < sc.n_tris; t += gridDim.x * blockDim.x) {
+        f3 a = mk3(sc.v0x[t], sc.v0y[t], sc.v0z[t]);
+        f3 b = mk3(sc.v1x[t], sc.v1y[t], sc.v1z[t]);
+        f3 c = mk3(sc.v2x[t], sc.v2y[t], sc.v2z[t]);
+        f3 m = (a + b + c) * (1.0f / 3.0f);
+        float r = fmaxf(len(a - m), fmaxf(len(b - m), len(c - m)));
+        float mag = fabsf(m.x) + fabsf(m.y) + fabsf(m.z) + r;
+        r = r * (1.0f + 9.6e-7f) + 3.9e-6f * mag;   // covers the FP32 error of eq. 9 at this distance
+        reinterpret_cast<float4*>(sc.tri_sphere)[t] = make_float4(m.x, m.y, m.z, r);
+        f3 e1 = b - a, e2 = c - a;
+        float4* mt = reinterpret_cast<float4*>(sc.tri_mt) + 3 * (size_t)t;
+        mt[0] = make_float4(a.x, a.y, a.z, 0.0f);
+        mt[1] = make_float4(e1.x, e1.y, e1.z, 0.0f);
+        mt[2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+    }
+}
+
+crsh_status prepare_scene_launch(const crsh_scene* sc, cudaStream_t s, const DeviceInfo& dev) {
+    const unsigned blocks = (sc->n_tris + 255) / 256;
+    const unsigned grid = blocks < (unsigned)dev.sms * 8 ? (blocks ? blocks : 1) : dev.sms * 8;
+    k_prepare<<<grid, 256, 0, s>>>(*sc);
+    return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
+}
+
+}  // namespace crsh

@@ -1,0 +1,179 @@
+// Shared device helpers of the CRSH library: status reporting, decoupled
+// look-back prefix sums (single-pass scans with bounded waits), warp scans,
+// small vector math.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "crsh.h"
+
+namespace crsh {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---- device status -------------------------------------------------------
+
+// First error wins: later errors never overwrite an earlier one.
+__device__ __forceinline__ void set_status(crsh_counters* c, unsigned code) {
+    if (c) atomicCAS(&c->status, 0u, code);
+}
+
+// ---- vector helpers ------------------------------------------------------
+
+struct f3 { float x, y, z; };
+__device__ __forceinline__ f3 mk3(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 operator+(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ f3 operator*(f3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 cross(f3 a, f3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float len(f3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ f3 unit(f3 a) { return a * rsqrtf(dot(a, a)); }
+// angle between two directions; accurate near 0 and pi
+__device__ __forceinline__ float angle(f3 a, f3 b) { return atan2f(len(cross(a, b)), dot(a, b)); }
+
+constexpr float PI_F = 3.14159265358979323846f;
+
+// ---- relaxed global loads/stores for look-back status words --------------
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed32(unsigned* p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ---- warp reductions / scans ---------------------------------------------
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// inclusive scan of 32-bit values over the warp
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned n = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---- decoupled look-back (single-pass prefix across tiles) ---------------
+//
+// Tiles are handed out in increasing order (atomic counter), so every tile a
+// block waits for has already been taken by a running block, which publishes
+// its own total before it waits on anyone.  Status word: bits 63:62 flag
+// (0 = not ready, 1 = tile total, 2 = inclusive prefix), bits 61:0 value.
+// Waits are bounded: after kSpinLimit polls the tile records
+// CRSH_ERR_TIMEOUT and continues with what it has.
+
+constexpr unsigned long long LB_AGG = 1ull << 62;
+constexpr unsigned long long LB_INC = 2ull << 62;
+constexpr unsigned long long LB_VAL = (1ull << 62) - 1;
+constexpr unsigned kSpinLimit = 1u << 22;
+
+// Called by all 32 lanes of ONE warp; returns the exclusive prefix of `tile`
+// (the same in every lane) and publishes the tile's inclusive prefix.
+__device__ __forceinline__ unsigned long long lookback_warp(unsigned long long* status, unsigned tile,
+                                                           unsigned long long aggregate,
+                                                           crsh_counters* ctr) {
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) st_relaxed(&status[0], LB_INC | aggregate);
+        return 0;
+    }
+    if (lane == 0) st_relaxed(&status[tile], LB_AGG | aggregate);
+    unsigned long long excl = 0;
+    long long k = (long long)tile - 1;
+    unsigned spins = 0;
+    while (true) {
+        long long idx = k - lane;
+        unsigned long long s = (idx >= 0) ? ld_relaxed(&status[idx]) : LB_INC;
+        while (__any_sync(FULL, (s >> 62) == 0)) {
+            if (++spins > kSpinLimit) {
+                if (lane == 0) set_status(ctr, CRSH_ERR_TIMEOUT);
+                if ((s >> 62) == 0) s = LB_INC;
+                break;
+            }
+            __nanosleep(32);
+            if ((s >> 62) == 0) s = ld_relaxed(&status[idx]);
+        }
+        unsigned inc = __ballot_sync(FULL, (s >> 62) == 2);
+        unsigned long long v = s & LB_VAL;
+        if (inc) {
+            int first = __ffs(inc) - 1;
+            excl += warp_sum64(lane <= first ? v : 0ull);
+            break;
+        }
+        excl += warp_sum64(v);
+        k -= 32;
+    }
+    if (lane == 0) st_relaxed(&status[tile], LB_INC | (excl + aggregate));
+    return excl;
+}
+
+// 32-bit status word variant for one thread (used per radix digit):
+// bits 31:30 flag, 29:0 value (counts below 2^30).
+constexpr unsigned LB32_AGG = 1u << 30;
+constexpr unsigned LB32_INC = 2u << 30;
+constexpr unsigned LB32_VAL = (1u << 30) - 1;
+
+__device__ __forceinline__ unsigned lookback_thread32(unsigned* status, unsigned tile, unsigned stride,
+                                                      unsigned aggregate, crsh_counters* ctr) {
+    if (tile == 0) {
+        st_relaxed32(&status[0], LB32_INC | aggregate);
+        return 0;
+    }
+    st_relaxed32(&status[(size_t)tile * stride], LB32_AGG | aggregate);
+    unsigned excl = 0;
+    unsigned spins = 0;
+    for (long long k = (long long)tile - 1; k >= 0; --k) {
+        unsigned s = ld_relaxed32(&status[(size_t)k * stride]);
+        while ((s >> 30) == 0) {
+            if (++spins > kSpinLimit) {
+                set_status(ctr, CRSH_ERR_TIMEOUT);
+                s = LB32_INC;
+                break;
+            }
+            __nanosleep(32);
+            s = ld_relaxed32(&status[(size_t)k * stride]);
+        }
+        excl += s & LB32_VAL;
+        if ((s >> 30) == 2) break;
+    }
+    st_relaxed32(&status[(size_t)tile * stride], LB32_INC | (excl + aggregate));
+    return excl;
+}
+
+// Hands out tiles in increasing order; returns the tile in every thread.
+__device__ __forceinline__ unsigned next_tile(unsigned* counter, unsigned* smem_slot) {
+    __syncthreads();
+    if (threadIdx.x == 0) *smem_slot = atomicAdd(counter, 1u);
+    __syncthreads();
+    return *smem_slot;
+}
+
+}  // namespace crsh

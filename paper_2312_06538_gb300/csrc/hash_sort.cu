@@ -1,0 +1,772 @@
+// Section 3.3.2-3.3.5: secondary ray generation, per-type hashing, trimming,
+// compression into chunks, radix sort of the chunks, decompression.
+//
+// GB300 design: one pass over the G-buffer generates, hashes and trims
+// (stable compaction by decoupled look-back, no second pass over the slots);
+// compression is one more compaction over the keys; the sort is a one-sweep
+// LSD radix sort (8-bit digits, one kernel per digit, digits that are the
+// same for every key skipped on the device) with stable per-warp multisplit
+// ranking; decompression and the gather of the sorted rays are one kernel.
+// Sizes stay on the device: every kernel runs a persistent grid and reads the
+// count it works on.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace crsh {
+
+// ---------------------------------------------------------------------------
+// FP32 ray generation with a fixed operation order (no contraction): the keys
+// derived from these rays are integers, decided in the paper's 32-bit
+// precision, and must not depend on how a compiler fuses operations.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fd(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float len3_rn(float x, float y, float z) {
+    return __fsqrt_rn(fa(fa(fm(x, x), fm(y, y)), fm(z, z)));
+}
+
+struct GenRay {
+    float o[3], d[3], tmax;
+    uint8_t type, light;
+};
+
+// Tables: theta thresholds cos(k pi / 2^tb) and phi thresholds tan(j pi / 2^pb),
+// rounded to FP32, built on the host and copied in through kernel parameters.
+struct HashDev {
+    const float* cosS;  // 2^stb entries
+    const float* tanS;  // 2^spb / 8 entries
+    const float* cosR;
+    const float* tanR;
+    float lo[3], hi[3];
+    unsigned stb, spb, cb, tb, pb;
+};
+
+// #{k in [1, B-1] : dz < T[k]}, T non-increasing: the largest such k (or 0).
+// Start from an approximate bin and move until the exact table condition holds.
+__device__ __forceinline__ unsigned theta_bin(float dz, const float* T, unsigned bits) {
+    const unsigned B = 1u << bits;
+    int b;
+    if (!(dz < 1.0f)) b = 0;
+    else if (!(dz > -1.0f)) b = (int)B - 1;
+    else b = (int)(acosf(dz) * ((float)B / PI_F));
+    b = min(max(b, 0), (int)B - 1);
+    while (b < (int)B - 1 && dz < __ldg(&T[b + 1])) ++b;
+    while (b > 0 && !(dz < __ldg(&T[b]))) --b;
+    return (unsigned)b;
+}
+
+// #{j in [1, M-1] : r >= T[j]} (strict = false) or r > T[j] (strict = true);
+// T increasing.
+__device__ __forceinline__ unsigned tan_count(float r, const float* T, unsigned M, bool strict) {
+    int j = (int)(atanf(r) * ((float)(4 * M) / PI_F));
+    j = min(max(j, 0), (int)M - 1);
+    auto ok = [&](int k) { float t = __ldg(&T[k]); return strict ? (r > t) : (r >= t); };
+    while (j < (int)M - 1 && ok(j + 1)) ++j;
+    while (j > 0 && !ok(j)) --j;
+    return (unsigned)j;
+}
+
+__device__ __forceinline__ unsigned phi_bin(float x, float y, const float* T, unsigned bits) {
+    const unsigned Bp = 1u << bits, M = Bp / 8, Q = Bp / 4;
+    unsigned q;
+    float a, b;
+    if (x > 0.0f && y >= 0.0f) { q = 0; a = x; b = y; }
+    else if (x <= 0.0f && y > 0.0f) { q = 1; a = y; b = -x; }
+    else if (x < 0.0f && y <= 0.0f) { q = 2; a = -x; b = -y; }
+    else if (x >= 0.0f && y < 0.0f) { q = 3; a = -y; b = x; }
+    else return 0;
+    unsigned psi;
+    if (b < a) psi = tan_count(fd(b, a), T, M, false);
+    else psi = 2 * M - 1 - tan_count(fd(a, b), T, M, true);
+    return q * Q + psi;
+}
+
+__device__ __forceinline__ unsigned interleave2(unsigned th, unsigned tb, unsigned ph, unsigned pb) {
+    unsigned code = 0, pos = 0, common = min(tb, pb);
+    for (unsigned b = 0; b < common; ++b) {
+        code |= ((ph >> b) & 1u) << pos++;
+        code |= ((th >> b) & 1u) << pos++;
+    }
+    for (unsigned b = common; b < pb; ++b) code |= ((ph >> b) & 1u) << pos++;
+    for (unsigned b = common; b < tb; ++b) code |= ((th >> b) & 1u) << pos++;
+    return code;
+}
+
+__device__ __forceinline__ unsigned cell_coord(float o, float lo, float hi, unsigned bits) {
+    const float cells = (float)(1u << bits);
+    float scale = fd(cells, fs(hi, lo));
+    float q = floorf(fm(fs(o, lo), scale));
+    if (!(q >= 0.0f)) return 0;
+    if (q > cells - 1.0f) return (1u << bits) - 1;
+    return (unsigned)q;
+}
+
+__device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z, unsigned bits) {
+    unsigned c = 0;
+    for (unsigned b = 0; b < bits; ++b)
+        c |= ((x >> b) & 1u) << (3 * b) | ((y >> b) & 1u) << (3 * b + 1) | ((z >> b) & 1u) << (3 * b + 2);
+    return c;
+}
+
+__device__ __forceinline__ unsigned ray_key(const GenRay& r, const HashDev& h) {
+    if (r.type == CRSH_RAY_SHADOW) {
+        unsigned th = theta_bin(r.d[2], h.cosS, h.stb);
+        unsigned ph = phi_bin(r.d[0], r.d[1], h.tanS, h.spb);
+        return ((unsigned)r.light << (h.stb + h.spb)) | interleave2(th, h.stb, ph, h.spb);
+    }
+    unsigned th = theta_bin(r.d[2], h.cosR, h.tb);
+    unsigned ph = phi_bin(r.d[0], r.d[1], h.tanR, h.pb);
+    unsigned cell = morton3(cell_coord(r.o[0], h.lo[0], h.hi[0], h.cb), cell_coord(r.o[1], h.lo[1], h.hi[1], h.cb),
+                            cell_coord(r.o[2], h.lo[2], h.hi[2], h.cb), h.cb);
+    return ((unsigned)r.type << 30) | (cell << (h.tb + h.pb)) | interleave2(th, h.tb, ph, h.pb);
+}
+
+// Generates the rays of one pixel in slot order; calls emit(ray) for each
+// existing ray.  Returns the count.  Mirrors the paper's ray types
+// (Section 3.3.2) with the origin of shadow rays inverted to the light.
+template <class Emit>
+__device__ __forceinline__ unsigned pixel_rays(const crsh_gbuffer& g, unsigned p, const float* lights,
+                                               unsigned n_lights, bool cull, Emit emit) {
+    if (!g.hit[p]) return 0;
+    const float P0 = g.px[p], P1 = g.py[p], P2 = g.pz[p];
+    const float N0 = g.nx[p], N1 = g.ny[p], N2 = g.nz[p];
+    const float I0 = g.ix[p], I1 = g.iy[p], I2 = g.iz[p];
+    unsigned cnt = 0;
+    for (unsigned k = 0; k < n_lights; ++k) {
+        const float L0 = __ldg(&lights[3 * k]), L1 = __ldg(&lights[3 * k + 1]), L2 = __ldg(&lights[3 * k + 2]);
+        const float v0 = fs(P0, L0), v1 = fs(P1, L1), v2 = fs(P2, L2);
+        float facing = fa(fa(fm(N0, v0), fm(N1, v1)), fm(N2, v2));
+        if (cull && !(facing < 0.0f)) continue;
+        float len = len3_rn(v0, v1, v2);
+        if (!(len > 0.0f)) continue;
+        GenRay r;
+        r.o[0] = L0; r.o[1] = L1; r.o[2] = L2;
+        r.d[0] = fd(v0, len); r.d[1] = fd(v1, len); r.d[2] = fd(v2, len);
+        r.tmax = fm(len, 0.9999f);
+        r.type = CRSH_RAY_SHADOW;
+        r.light = (uint8_t)k;
+        emit(r);
+        ++cnt;
+    }
+    const unsigned m = g.material[p];
+    if (m != CRSH_MAT_MIRROR && m != CRSH_MAT_GLASS) return cnt;
+    const float c = fa(fa(fm(I0, N0), fm(I1, N1)), fm(I2, N2));
+    const float off = (c > 0.0f) ? -1e-4f : 1e-4f;
+    {
+        const float two_c = fm(2.0f, c);
+        const float r0 = fs(I0, fm(two_c, N0)), r1 = fs(I1, fm(two_c, N1)), r2 = fs(I2, fm(two_c, N2));
+        const float rl = len3_rn(r0, r1, r2);
+        GenRay r;
+        r.o[0] = fa(P0, fm(off, N0)); r.o[1] = fa(P1, fm(off, N1)); r.o[2] = fa(P2, fm(off, N2));
+        r.d[0] = fd(r0, rl); r.d[1] = fd(r1, rl); r.d[2] = fd(r2, rl);
+        r.tmax = __int_as_float(0x7f800000);
+        r.type = CRSH_RAY_REFLECTION;
+        r.light = 0;
+        emit(r);
+        ++cnt;
+    }
+    if (m == CRSH_MAT_GLASS) {
+        const float ior = 1.5f;
+        float eta, cosi, M0, M1, M2;
+        if (c < 0.0f) { eta = fd(1.0f, ior); cosi = -c; M0 = N0; M1 = N1; M2 = N2; }
+        else { eta = ior; cosi = c; M0 = -N0; M1 = -N1; M2 = -N2; }
+        const float sin2 = fs(1.0f, fm(cosi, cosi));
+        const float k = fs(1.0f, fm(fm(eta, eta), sin2));
+        if (!(k < 0.0f)) {
+            const float coef = fs(fm(eta, cosi), __fsqrt_rn(k));
+            const float t0 = fa(fm(eta, I0), fm(coef, M0));
+            const float t1 = fa(fm(eta, I1), fm(coef, M1));
+            const float t2 = fa(fm(eta, I2), fm(coef, M2));
+            const float tl = len3_rn(t0, t1, t2);
+            GenRay r;
+            r.o[0] = fs(P0, fm(off, N0)); r.o[1] = fs(P1, fm(off, N1)); r.o[2] = fs(P2, fm(off, N2));
+            r.d[0] = fd(t0, tl); r.d[1] = fd(t1, tl); r.d[2] = fd(t2, tl);
+            r.tmax = __int_as_float(0x7f800000);
+            r.type = CRSH_RAY_REFRACTION;
+            r.light = 0;
+            emit(r);
+            ++cnt;
+        }
+    }
+    return cnt;
+}
+
+struct GenOut {
+    float *ox, *oy, *oz, *dx, *dy, *dz, *tmax;
+    uint8_t* type;
+    uint32_t* pixel;
+    uint32_t* key;   // generation-order keys
+    uint32_t* val;   // = generation index
+    uint32_t capacity;
+};
+
+__device__ __forceinline__ void store_ray(const GenOut& o, unsigned pos, const GenRay& r, unsigned key,
+                                          unsigned pixel) {
+    o.ox[pos] = r.o[0]; o.oy[pos] = r.o[1]; o.oz[pos] = r.o[2];
+    o.dx[pos] = r.d[0]; o.dy[pos] = r.d[1]; o.dz[pos] = r.d[2];
+    o.tmax[pos] = r.tmax;
+    o.type[pos] = r.type;
+    o.pixel[pos] = pixel;
+    o.key[pos] = key;
+    o.val[pos] = pos;
+}
+
+constexpr int GEN_BLOCK = 256;
+
+// One thread per pixel; stable trimming of empty slots by block scan plus
+// decoupled look-back across tiles.
+__global__ void __launch_bounds__(GEN_BLOCK) k_gen_gbuffer(crsh_gbuffer g, const float* lights, unsigned n_lights,
+                                                           int cull, HashDev h, GenOut out, unsigned* n_out,
+                                                           unsigned long long* status, unsigned* tile_ctr,
+                                                           crsh_counters* ctr) {
+    __shared__ unsigned s_tile;
+    __shared__ unsigned s_warp[GEN_BLOCK / 32 + 1];
+    __shared__ unsigned long long s_prefix;
+    const unsigned n_tiles = (g.n_pixels + GEN_BLOCK - 1) / GEN_BLOCK;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        const unsigned tile = next_tile(tile_ctr, &s_tile);
+        if (tile >= n_tiles) break;
+        const unsigned p = tile * GEN_BLOCK + threadIdx.x;
+        unsigned cnt = 0;
+        if (p < g.n_pixels) cnt = pixel_rays(g, p, lights, n_lights, cull != 0, [](const GenRay&) {});
+        // block exclusive scan
+        unsigned inc = warp_incl_scan(cnt);
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned w = lane < GEN_BLOCK / 32 ? s_warp[lane] : 0;
+            unsigned wi = warp_incl_scan(w);
+            if (lane < GEN_BLOCK / 32) s_warp[lane] = wi - w;
+            unsigned total = __shfl_sync(FULL, wi, GEN_BLOCK / 32 - 1);
+            unsigned long long pre = lookback_warp(status, tile, total, ctr);
+            if (lane == 0) {
+                s_prefix = pre;
+                if (tile == n_tiles - 1) {
+                    unsigned long long all = pre + total;
+                    ctr->rays = all;
+                    *n_out = (unsigned)min(all, (unsigned long long)out.capacity);
+                    if (all > out.capacity) set_status(ctr, CRSH_ERR_CAPACITY);
+                }
+            }
+        }
+        __syncthreads();
+        unsigned long long pos = s_prefix + s_warp[warp] + inc - cnt;
+        if (cnt) {
+            pixel_rays(g, p, lights, n_lights, cull != 0, [&](const GenRay& r) {
+                if (pos < out.capacity) store_ray(out, (unsigned)pos, r, ray_key(r, h), p);
+                ++pos;
+            });
+        }
+    }
+}
+
+// Prebuilt rays: hash and copy (every input is a ray, order kept).
+__global__ void k_gen_rays(crsh_rays_in in, HashDev h, GenOut out, unsigned* n_out, crsh_counters* ctr) {
+    const unsigned n = min(in.n, out.capacity);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->rays = in.n;
+        *n_out = n;
+        if (in.n > out.capacity) set_status(ctr, CRSH_ERR_CAPACITY);
+    }
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        GenRay r;
+        r.o[0] = in.ox[i]; r.o[1] = in.oy[i]; r.o[2] = in.oz[i];
+        r.d[0] = in.dx[i]; r.d[1] = in.dy[i]; r.d[2] = in.dz[i];
+        r.tmax = in.tmax[i];
+        r.type = in.type[i];
+        r.light = in.light ? in.light[i] : 0;
+        if (r.type > CRSH_RAY_REFRACTION ||
+            (r.type == CRSH_RAY_SHADOW && (unsigned)r.light >= (1u << (30 - h.stb - h.spb)))) {
+            set_status(ctr, CRSH_ERR_BAD_INPUT);
+            r.type = CRSH_RAY_REFLECTION;
+        }
+        store_ray(out, i, r, ray_key(r, h), i);
+    }
+}
+
+// Loads host-built threshold tables through kernel parameters (capturable,
+// no pageable copies).
+__global__ void k_put_table(TableChunk c, float* dst) {
+    for (unsigned i = threadIdx.x; i < c.count; i += blockDim.x) dst[c.offset + i] = c.v[i];
+}
+
+// ---------------------------------------------------------------------------
+// Section 3.3.3: compression.  Head flag where the key differs from the
+// previous one; a stable compaction of the heads gives chunk key and base.
+// ---------------------------------------------------------------------------
+constexpr int CMP_BLOCK = 256, CMP_ITEMS = 4, CMP_TILE = CMP_BLOCK * CMP_ITEMS;
+
+__global__ void __launch_bounds__(CMP_BLOCK) k_chunk(const uint32_t* key, const unsigned* n_ptr, uint32_t* ckey,
+                                                     uint32_t* cval, uint32_t* cbase, unsigned* c_out,
+                                                     unsigned long long* status, unsigned* tile_ctr,
+                                                     crsh_counters* ctr) {
+    __shared__ unsigned s_tile;
+    __shared__ unsigned s_cnt[CMP_ITEMS][CMP_BLOCK / 32];
+    __shared__ unsigned long long s_prefix;
+    const unsigned n = *n_ptr;
+    const unsigned n_tiles = (n + CMP_TILE - 1) / CMP_TILE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        *c_out = 0;
+        cbase[0] = 0;
+        ctr->chunks = 0;
+    }
+    for (;;) {
+        const unsigned tile = next_tile(tile_ctr, &s_tile);
+        if (tile >= n_tiles) break;
+        bool f[CMP_ITEMS];
+        unsigned bal[CMP_ITEMS];
+        unsigned k[CMP_ITEMS];
+#pragma unroll
+        for (int i = 0; i < CMP_ITEMS; ++i) {
+            unsigned e = tile * CMP_TILE + i * CMP_BLOCK + threadIdx.x;
+            f[i] = false;
+            if (e < n) {
+                k[i] = key[e];
+                f[i] = (e == 0) || (key[e - 1] != k[i]);
+            }
+            bal[i] = __ballot_sync(FULL, f[i]);
+            if (lane == 0) s_cnt[i][warp] = __popc(bal[i]);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // scan the (item, warp) counts in element order
+            unsigned v = s_cnt[lane / (CMP_BLOCK / 32)][lane % (CMP_BLOCK / 32)];
+            unsigned inc = warp_incl_scan(v);
+            s_cnt[lane / (CMP_BLOCK / 32)][lane % (CMP_BLOCK / 32)] = inc - v;
+            unsigned total = __shfl_sync(FULL, inc, 31);
+            unsigned long long pre = lookback_warp(status, tile, total, ctr);
+            if (lane == 0) {
+                s_prefix = pre;
+                if (tile == n_tiles - 1) {
+                    unsigned all = (unsigned)(pre + total);
+                    *c_out = all;
+                    cbase[all] = n;
+                    ctr->chunks = all;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < CMP_ITEMS; ++i) {
+            if (f[i]) {
+                unsigned pos = (unsigned)s_prefix + s_cnt[i][warp] + __popc(bal[i] & lanemask_lt());
+                unsigned e = tile * CMP_TILE + i * CMP_BLOCK + threadIdx.x;
+                ckey[pos] = k[i];
+                cval[pos] = pos;
+                cbase[pos] = e;
+            }
+        }
+    }
+}
+static_assert(CMP_ITEMS * (CMP_BLOCK / 32) == 32, "one warp scans the per-warp counts");
+
+// ---------------------------------------------------------------------------
+// Section 3.3.4: radix sort (LSD, 8-bit digits, one sweep per digit).
+// ---------------------------------------------------------------------------
+constexpr int RS_BLOCK = 256, RS_WARPS = RS_BLOCK / 32, RS_KPT = 8, RS_TILE = RS_BLOCK * RS_KPT;
+
+__global__ void k_radix_hist(const uint32_t* key, const unsigned* n_ptr, unsigned* hist /* 4 x 256 */) {
+    __shared__ unsigned s_h[4][256];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned n = *n_ptr;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned k = key[i];
+        atomicAdd(&s_h[0][k & 255], 1u);
+        atomicAdd(&s_h[1][(k >> 8) & 255], 1u);
+        atomicAdd(&s_h[2][(k >> 16) & 255], 1u);
+        atomicAdd(&s_h[3][k >> 24], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+        unsigned v = (&s_h[0][0])[i];
+        if (v) atomicAdd(&hist[i], v);
+    }
+}
+
+// plan[p]: 0 = pass skipped (one digit holds every key), else 1 + source
+// buffer (0 = A, 1 = B); plan[4] = buffer holding the sorted result.
+// offs[p][d] = keys with a smaller digit d at pass p.
+__global__ void k_radix_plan(const unsigned* hist, const unsigned* n_ptr, unsigned* offs, unsigned* plan,
+                             int sort_enabled) {
+    __shared__ unsigned s_triv[4];
+    const unsigned n = *n_ptr;
+    const int d = threadIdx.x;   // 256 threads
+    if (d < 4) s_triv[d] = 0;
+    __syncthreads();
+    for (int p = 0; p < 4; ++p) {
+        unsigned v = hist[p * 256 + d];
+        if (v == n) s_triv[p] = 1;   // includes n == 0
+        // exclusive scan over 256 digits
+        __shared__ unsigned s_w[8];
+        unsigned inc = warp_incl_scan(v);
+        if ((d & 31) == 31) s_w[d >> 5] = inc;
+        __syncthreads();
+        unsigned wpre = 0;
+        for (int w = 0; w < (d >> 5); ++w) wpre += s_w[w];
+        offs[p * 256 + d] = wpre + inc - v;
+        __syncthreads();
+    }
+    if (d == 0) {
+        unsigned cur = 0;
+        for (int p = 0; p < 4; ++p) {
+            if (!sort_enabled || s_triv[p]) plan[p] = 0;
+            else { plan[p] = 1 + cur; cur ^= 1u; }
+        }
+        plan[4] = cur;
+    }
+}
+
+__global__ void __launch_bounds__(RS_BLOCK) k_radix_pass(int pass, uint32_t* kA, uint32_t* vA, uint32_t* kB,
+                                                         uint32_t* vB, const unsigned* n_ptr, const unsigned* offs,
+                                                         const unsigned* plan, unsigned* status,
+                                                         unsigned* tile_ctr, crsh_counters* ctr) {
+    const unsigned pl = plan[pass];
+    if (pl == 0) return;
+    const uint32_t* sk = (pl == 1) ? kA : kB;
+    const uint32_t* sv = (pl == 1) ? vA : vB;
+    uint32_t* dk = (pl == 1) ? kB : kA;
+    uint32_t* dv = (pl == 1) ? vB : vA;
+    const unsigned shift = 8 * pass;
+    __shared__ unsigned s_tile;
+    __shared__ unsigned s_wh[RS_WARPS][256];
+    __shared__ unsigned s_base[256];
+    const unsigned n = *n_ptr;
+    const unsigned n_tiles = (n + RS_TILE - 1) / RS_TILE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        const unsigned tile = next_tile(tile_ctr, &s_tile);
+        if (tile >= n_tiles) break;
+        for (int i = lane; i < 256; i += 32) s_wh[warp][i] = 0;
+        __syncwarp();
+        unsigned key[RS_KPT], val[RS_KPT], rank[RS_KPT];
+        const unsigned base = tile * RS_TILE + warp * (32 * RS_KPT);
+#pragma unroll
+        for (int r = 0; r < RS_KPT; ++r) {
+            unsigned e = base + r * 32 + lane;
+            bool valid = e < n;
+            key[r] = valid ? sk[e] : 0;
+            val[r] = valid ? sv[e] : 0;
+            unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u;
+            unsigned peers = __match_any_sync(FULL, d);
+            unsigned pre = valid ? s_wh[warp][d] : 0;
+            rank[r] = pre + __popc(peers & lanemask_lt());
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) s_wh[warp][d] = pre + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {   // thread = digit: exclusive over warps, tile total, look-back over tiles
+            const int d = threadIdx.x;
+            unsigned run = 0;
+            for (int w = 0; w < RS_WARPS; ++w) {
+                unsigned c = s_wh[w][d];
+                s_wh[w][d] = run;
+                run += c;
+            }
+            unsigned excl = lookback_thread32(status + d, tile, 256, run, ctr);
+            s_base[d] = offs[pass * 256 + d] + excl;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RS_KPT; ++r) {
+            unsigned e = base + r * 32 + lane;
+            if (e < n) {
+                unsigned d = (key[r] >> shift) & 255u;
+                unsigned pos = s_base[d] + s_wh[warp][d] + rank[r];
+                dk[pos] = key[r];
+                dv[pos] = val[r];
+            }
+        }
+    }
+}
+static_assert(RS_BLOCK == 256, "one thread per digit");
+
+// ---------------------------------------------------------------------------
+// Section 3.3.5: decompression.  Chunk sizes in sorted order, exclusive scan
+// (the skeleton), then every sorted position finds its chunk.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_BLOCK = 256, SCAN_ITEMS = 4, SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_pos(const uint32_t* kA, const uint32_t* vA, const uint32_t* kB,
+                                                          const uint32_t* vB, const unsigned* plan,
+                                                          const uint32_t* cbase, const unsigned* c_ptr,
+                                                          uint32_t* cpos, unsigned long long* status,
+                                                          unsigned* tile_ctr, crsh_counters* ctr) {
+    __shared__ unsigned s_tile;
+    __shared__ unsigned s_warp[SCAN_BLOCK / 32];
+    __shared__ unsigned long long s_prefix;
+    const uint32_t* sv = plan[4] ? vB : vA;
+    const unsigned C = *c_ptr;
+    const unsigned n_tiles = (C + SCAN_TILE - 1) / SCAN_TILE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        const unsigned tile = next_tile(tile_ctr, &s_tile);
+        if (tile >= n_tiles) break;
+        // blocked: thread handles SCAN_ITEMS consecutive chunks
+        const unsigned e0 = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+        unsigned sz[SCAN_ITEMS], sum = 0;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            unsigned e = e0 + i;
+            sz[i] = 0;
+            if (e < C) {
+                unsigned c = sv[e];
+                sz[i] = cbase[c + 1] - cbase[c];
+            }
+            sum += sz[i];
+        }
+        unsigned inc = warp_incl_scan(sum);
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned w = lane < SCAN_BLOCK / 32 ? s_warp[lane] : 0;
+            unsigned wi = warp_incl_scan(w);
+            if (lane < SCAN_BLOCK / 32) s_warp[lane] = wi - w;
+            unsigned total = __shfl_sync(FULL, wi, SCAN_BLOCK / 32 - 1);
+            unsigned long long pre = lookback_warp(status, tile, total, ctr);
+            if (lane == 0) s_prefix = pre;
+        }
+        __syncthreads();
+        unsigned run = (unsigned)s_prefix + s_warp[warp] + inc - sum;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            unsigned e = e0 + i;
+            if (e < C) cpos[e] = run;
+            run += sz[i];
+        }
+    }
+}
+
+struct SortedOut {
+    float *ox, *oy, *oz, *dx, *dy, *dz, *tmax;
+    uint8_t* type;
+    uint32_t *ray_id, *pixel, *keys;
+};
+
+// mode 0: generation order; 1: sorted (value = ray index); 2: sorted chunks.
+__global__ void k_gather(int mode, GenOut gen, const uint32_t* kA, const uint32_t* vA, const uint32_t* kB,
+                         const uint32_t* vB, const unsigned* plan, const uint32_t* cbase, const uint32_t* cpos,
+                         const unsigned* c_ptr, const unsigned* n_ptr, SortedOut out) {
+    const unsigned n = *n_ptr;
+    const unsigned C = (mode == 2) ? *c_ptr : 0;
+    const uint32_t* sv = (mode != 0 && plan[4]) ? vB : vA;
+    const uint32_t* sk = (mode != 0 && plan[4]) ? kB : kA;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned src, key;
+        if (mode == 0) {
+            src = i;
+            key = gen.key[i];
+        } else if (mode == 1) {
+            src = sv[i];
+            key = sk[i];
+        } else {
+            // last sorted chunk whose start is <= i
+            unsigned lo = 0, hi = C - 1;
+            while (lo < hi) {
+                unsigned mid = lo + (hi - lo + 1) / 2;
+                if (cpos[mid] <= i) lo = mid; else hi = mid - 1;
+            }
+            src = cbase[sv[lo]] + (i - cpos[lo]);
+            key = sk[lo];
+        }
+        out.ox[i] = gen.ox[src]; out.oy[i] = gen.oy[src]; out.oz[i] = gen.oz[src];
+        out.dx[i] = gen.dx[src]; out.dy[i] = gen.dy[src]; out.dz[i] = gen.dz[src];
+        out.tmax[i] = gen.tmax[src];
+        out.type[i] = gen.type[src];
+        out.pixel[i] = gen.pixel[src];
+        out.ray_id[i] = src;
+        out.keys[i] = key;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+namespace {
+struct Carve {
+    char* base;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+struct HashWs {
+    GenOut gen;
+    uint32_t *chK, *chV, *chBase, *chPos, *altK, *altV;
+    float* tables;
+    // control region (zeroed per call)
+    char* ctl_begin;
+    size_t ctl_bytes;
+    size_t total;
+    unsigned* tile_ctr;      // 8 counters
+    unsigned* counts;        // [0] chunk count
+    unsigned* hist;          // 4 x 256
+    unsigned* offs;          // 4 x 256
+    unsigned* plan;          // 5
+    unsigned long long* st_gen;
+    unsigned long long* st_chunk;
+    unsigned long long* st_pos;
+    unsigned* st_radix;      // 4 passes x tiles x 256
+};
+
+size_t table_floats() { return (1u << 13) * 2 + (1u << 13) / 8 * 2; }
+
+HashWs carve_hash(void* ws, uint32_t cap, uint32_t max_pixels) {
+    Carve c{reinterpret_cast<char*>(ws)};
+    HashWs w{};
+    w.gen.ox = c.take<float>(cap); w.gen.oy = c.take<float>(cap); w.gen.oz = c.take<float>(cap);
+    w.gen.dx = c.take<float>(cap); w.gen.dy = c.take<float>(cap); w.gen.dz = c.take<float>(cap);
+    w.gen.tmax = c.take<float>(cap);
+    w.gen.type = c.take<uint8_t>(cap);
+    w.gen.pixel = c.take<uint32_t>(cap);
+    w.gen.key = c.take<uint32_t>(cap);
+    w.gen.val = c.take<uint32_t>(cap);
+    w.gen.capacity = cap;
+    w.chK = c.take<uint32_t>(cap);
+    w.chV = c.take<uint32_t>(cap);
+    w.chBase = c.take<uint32_t>((size_t)cap + 1);
+    w.chPos = c.take<uint32_t>(cap);
+    w.altK = c.take<uint32_t>(cap);
+    w.altV = c.take<uint32_t>(cap);
+    w.tables = c.take<float>(table_floats());
+    c.off = (c.off + 255) & ~size_t(255);
+    size_t ctl0 = c.off;
+    w.tile_ctr = c.take<unsigned>(16);
+    w.counts = c.take<unsigned>(4);
+    w.hist = c.take<unsigned>(1024);
+    w.offs = c.take<unsigned>(1024);
+    w.plan = c.take<unsigned>(8);
+    const size_t gen_tiles = ((size_t)max_pixels + GEN_BLOCK - 1) / GEN_BLOCK + 1;
+    const size_t cmp_tiles = ((size_t)cap + CMP_TILE - 1) / CMP_TILE + 1;
+    const size_t rs_tiles = ((size_t)cap + RS_TILE - 1) / RS_TILE + 1;
+    const size_t sc_tiles = ((size_t)cap + SCAN_TILE - 1) / SCAN_TILE + 1;
+    w.st_gen = c.take<unsigned long long>(gen_tiles);
+    w.st_chunk = c.take<unsigned long long>(cmp_tiles);
+    w.st_pos = c.take<unsigned long long>(sc_tiles);
+    w.st_radix = c.take<unsigned>(4 * rs_tiles * 256);
+    w.ctl_begin = ws ? reinterpret_cast<char*>(ws) + ctl0 : nullptr;
+    w.ctl_bytes = c.off - ctl0;
+    w.total = c.off + 256;
+    return w;
+}
+}  // namespace
+
+size_t hash_sort_workspace(uint32_t cap, uint32_t max_pixels) {
+    return carve_hash(nullptr, cap, max_pixels).total;
+}
+
+static void put_table(float* dst, const float* src, unsigned count, cudaStream_t s) {
+    for (unsigned off = 0; off < count; off += TableChunk::kMax) {
+        TableChunk c;
+        c.offset = off;
+        c.count = count - off < TableChunk::kMax ? count - off : TableChunk::kMax;
+        for (unsigned i = 0; i < c.count; ++i) c.v[i] = src[off + i];
+        k_put_table<<<1, 256, 0, s>>>(c, dst);
+    }
+}
+
+crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, const float* lights, uint32_t n_lights,
+                             const crsh_hash_params* hp, crsh_rays* out, uint32_t* keys_out, uint32_t* n_out,
+                             crsh_counters* ctr, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev) {
+    const uint32_t cap = out->capacity;
+    const uint32_t max_pixels = gb ? gb->n_pixels : 0;
+    if (ws_bytes < hash_sort_workspace(cap, max_pixels)) return CRSH_ERR_INVALID_ARG;
+    HashWs w = carve_hash(ws, cap, max_pixels);
+
+    // threshold tables, FP32-rounded from double libm values
+    const unsigned BS = 1u << hp->shadow_theta_bits, MS = (1u << hp->shadow_phi_bits) / 8;
+    const unsigned BR = 1u << hp->sec_theta_bits, MR = (1u << hp->sec_phi_bits) / 8;
+    float* tcosS = w.tables;
+    float* ttanS = tcosS + BS;
+    float* tcosR = ttanS + MS;
+    float* ttanR = tcosR + BR;
+    {
+        static thread_local float host[(1u << 13) * 2 + (1u << 13) / 8 * 2];
+        const double pi = 3.14159265358979323846;
+        unsigned o = 0;
+        for (unsigned k = 0; k < BS; ++k) host[o++] = (float)cos((double)k * pi / (double)BS);
+        for (unsigned j = 0; j < MS; ++j) host[o++] = (float)tan((double)j * (pi / 4.0) / (double)MS);
+        for (unsigned k = 0; k < BR; ++k) host[o++] = (float)cos((double)k * pi / (double)BR);
+        for (unsigned j = 0; j < MR; ++j) host[o++] = (float)tan((double)j * (pi / 4.0) / (double)MR);
+        put_table(w.tables, host, o, s);
+    }
+    HashDev h;
+    h.cosS = tcosS; h.tanS = ttanS; h.cosR = tcosR; h.tanR = ttanR;
+    for (int a = 0; a < 3; ++a) { h.lo[a] = hp->lo[a]; h.hi[a] = hp->hi[a]; }
+    h.stb = hp->shadow_theta_bits; h.spb = hp->shadow_phi_bits;
+    h.cb = hp->sec_cell_bits; h.tb = hp->sec_theta_bits; h.pb = hp->sec_phi_bits;
+
+    if (cudaMemsetAsync(w.ctl_begin, 0, w.ctl_bytes, s) != cudaSuccess) return CRSH_ERR_CUDA;
+    if (cudaMemsetAsync(ctr, 0, sizeof(crsh_counters), s) != cudaSuccess) return CRSH_ERR_CUDA;
+    if (cudaMemsetAsync(n_out, 0, sizeof(uint32_t), s) != cudaSuccess) return CRSH_ERR_CUDA;
+
+    const int persist = dev.sms * 8;
+    if (gb) {
+        const unsigned tiles = (gb->n_pixels + GEN_BLOCK - 1) / GEN_BLOCK;
+        const unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
+        k_gen_gbuffer<<<grid, GEN_BLOCK, 0, s>>>(*gb, lights, n_lights, (int)hp->shadow_cull, h, w.gen, n_out,
+                                                 w.st_gen, &w.tile_ctr[0], ctr);
+    } else {
+        unsigned blocks = (in->n + 255) / 256;
+        if (blocks > (unsigned)persist) blocks = persist;
+        if (blocks == 0) blocks = 1;
+        k_gen_rays<<<blocks, 256, 0, s>>>(*in, h, w.gen, n_out, ctr);
+    }
+
+    const bool sort = hp->sort != 0;
+    const bool compress = sort && hp->compress != 0;
+    const unsigned cap_tiles_rs = (cap + RS_TILE - 1) / RS_TILE;
+    uint32_t *kA = w.gen.key, *vA = w.gen.val;
+    const unsigned* cnt_ptr = n_out;
+    if (compress) {
+        unsigned tiles = (cap + CMP_TILE - 1) / CMP_TILE;
+        unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
+        k_chunk<<<grid, CMP_BLOCK, 0, s>>>(w.gen.key, n_out, w.chK, w.chV, w.chBase, &w.counts[0], w.st_chunk,
+                                           &w.tile_ctr[1], ctr);
+        kA = w.chK;
+        vA = w.chV;
+        cnt_ptr = &w.counts[0];
+    }
+    if (sort) {
+        k_radix_hist<<<dev.sms * 2, 256, 0, s>>>(kA, cnt_ptr, w.hist);
+        k_radix_plan<<<1, 256, 0, s>>>(w.hist, cnt_ptr, w.offs, w.plan, 1);
+        unsigned grid = cap_tiles_rs < (unsigned)(dev.sms * 4) ? (cap_tiles_rs ? cap_tiles_rs : 1) : dev.sms * 4;
+        const size_t rs_tiles = (size_t)cap_tiles_rs + 1;
+        for (int p = 0; p < 4; ++p)
+            k_radix_pass<<<grid, RS_BLOCK, 0, s>>>(p, kA, vA, w.altK, w.altV, cnt_ptr, w.offs, w.plan,
+                                                    w.st_radix + (size_t)p * rs_tiles * 256, &w.tile_ctr[2 + p], ctr);
+    } else {
+        k_radix_plan<<<1, 256, 0, s>>>(w.hist, cnt_ptr, w.offs, w.plan, 0);
+    }
+    if (compress) {
+        unsigned tiles = (cap + SCAN_TILE - 1) / SCAN_TILE;
+        unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
+        k_chunk_pos<<<grid, SCAN_BLOCK, 0, s>>>(kA, vA, w.altK, w.altV, w.plan, w.chBase, cnt_ptr, w.chPos,
+                                                 w.st_pos, &w.tile_ctr[6], ctr);
+    }
+    SortedOut so{out->ox, out->oy, out->oz, out->dx, out->dy, out->dz, out->tmax, out->type,
+                 out->ray_id, out->pixel, keys_out};
+    {
+        unsigned blocks = (cap + 255) / 256;
+        if (blocks > (unsigned)persist) blocks = persist;
+        if (blocks == 0) blocks = 1;
+        const int mode = !sort ? 0 : (compress ? 2 : 1);
+        k_gather<<<blocks, 256, 0, s>>>(mode, w.gen, kA, vA, w.altK, w.altV, w.plan, w.chBase, w.chPos, cnt_ptr,
+                                        n_out, so);
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
+}
+
+}  // namespace crsh

@@ -1,0 +1,271 @@
+// Section 3.3.8: final ray-triangle tests (Moller-Trumbore [Mol97]) over the
+// level-1 (node, triangle) pairs, closest hit per ray; and the N x M brute
+// force of Section 1 built on the same test, for comparison.
+//
+// GB300 design.  The level-1 pair list is cut into fixed chunks of pairs, one
+// per warp task, so long and short triangle lists balance across the 152 SMs.
+// In a warp, lane = (ray slot r < B, stream s < 32/B): the B rays of the
+// current node sit in registers; a group of up to 32 triangles of that node is
+// fetched once (one triangle per lane, 48 bytes, L2-resident) into shared
+// memory and each stream walks every (32/B)-th triangle against its ray.  The
+// per-ray best is a packed (t bits, triangle id) 64-bit key, reduced across
+// streams by shuffles and published with one atomicMin per ray per chunk, so
+// the result does not depend on scheduling.  A last pass recomputes (t, u, v)
+// of the winning triangle with the same test and scatters hits to the rays'
+// generation order.  Decisions (which triangle is closest) are FP32; the
+// reported (t, u, v) of the winner are recomputed in FP64 from the FP32 inputs.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace crsh {
+
+// Moller-Trumbore in FP32 with an explicit operation sequence (fused
+// multiply-adds written out), so every kernel that calls it gets the same
+// bits.  Two-sided; a zero determinant fails every range test below through
+// the infinite reciprocal; inclusive edges; 0 < t <= t_max.
+__device__ __forceinline__ bool mt_test(float ox, float oy, float oz, float dx, float dy, float dz, float tmax,
+                                        float4 a, float4 e1, float4 e2, float& t, float& u, float& v) {
+    const float px = __fmaf_rn(dy, e2.z, __fmul_rn(-dz, e2.y));
+    const float py = __fmaf_rn(dz, e2.x, __fmul_rn(-dx, e2.z));
+    const float pz = __fmaf_rn(dx, e2.y, __fmul_rn(-dy, e2.x));
+    const float det = __fmaf_rn(e1.x, px, __fmaf_rn(e1.y, py, __fmul_rn(e1.z, pz)));
+    const float inv = __frcp_rn(det);
+    const float sx = __fsub_rn(ox, a.x), sy = __fsub_rn(oy, a.y), sz = __fsub_rn(oz, a.z);
+    u = __fmul_rn(__fmaf_rn(sx, px, __fmaf_rn(sy, py, __fmul_rn(sz, pz))), inv);
+    const float qx = __fmaf_rn(sy, e1.z, __fmul_rn(-sz, e1.y));
+    const float qy = __fmaf_rn(sz, e1.x, __fmul_rn(-sx, e1.z));
+    const float qz = __fmaf_rn(sx, e1.y, __fmul_rn(-sy, e1.x));
+    v = __fmul_rn(__fmaf_rn(dx, qx, __fmaf_rn(dy, qy, __fmul_rn(dz, qz))), inv);
+    t = __fmul_rn(__fmaf_rn(e2.x, qx, __fmaf_rn(e2.y, qy, __fmul_rn(e2.z, qz))), inv);
+    return (u >= 0.0f) & (v >= 0.0f) & (__fadd_rn(u, v) <= 1.0f) & (t > 0.0f) & (t <= tmax);
+}
+
+__device__ __forceinline__ unsigned long long hit_key(float t, unsigned tri) {
+    return ((unsigned long long)__float_as_uint(t) << 32) | tri;
+}
+constexpr unsigned long long NO_HIT = ~0ull;
+
+struct RaysDev {
+    const float *ox, *oy, *oz, *dx, *dy, *dz, *tmax;
+    const uint32_t* ray_id;
+};
+
+constexpr int CH_WARPS = 4, CH_BLOCK = CH_WARPS * 32, CH_CHUNK = 512;
+
+template <int B>
+__global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, const uint32_t* ptri,
+                                                      const unsigned* p_count, unsigned long long p_cap,
+                                                      RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
+                                                      unsigned long long* best, crsh_counters* ctr) {
+    constexpr int S = 32 / B;
+    __shared__ float4 s_tri[CH_WARPS][32][3];
+    const unsigned P = (unsigned)min((unsigned long long)*p_count, p_cap);
+    const unsigned N = *n_ptr;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = lane % B, sidx = lane / B;
+    const unsigned gw = blockIdx.x * CH_WARPS + warp, nw = gridDim.x * CH_WARPS;
+    unsigned long long n_tests = 0, n_hits = 0;
+    for (unsigned q0 = gw * CH_CHUNK; q0 < P; q0 += nw * CH_CHUNK) {
+        const unsigned q1 = min(q0 + CH_CHUNK, P);
+        unsigned cur = 0xffffffffu, ray = 0;
+        bool rvalid = false;
+        float ox = 0, oy = 0, oz = 0, dx = 0, dy = 0, dz = 0, tmax = 0;
+        unsigned long long bk = NO_HIT;
+        auto flush = [&]() {
+            unsigned long long k = bk;
+#pragma unroll
+            for (int o = B; o < 32; o <<= 1) {
+                unsigned long long other = __shfl_xor_sync(FULL, k, o);
+                k = other < k ? other : k;
+            }
+            if (rvalid && sidx == 0 && k != NO_HIT) atomicMin(&best[ray], k);
+        };
+        unsigned q = q0;
+        while (q < q1) {
+            const unsigned node = pnode[q];   // same address in every lane
+            if (node != cur) {
+                flush();
+                cur = node;
+                ray = node * B + r;
+                rvalid = ray < N;
+                if (rvalid) {
+                    ox = rays.ox[ray]; oy = rays.oy[ray]; oz = rays.oz[ray];
+                    dx = rays.dx[ray]; dy = rays.dy[ray]; dz = rays.dz[ray];
+                    tmax = rays.tmax[ray];
+                }
+                bk = NO_HIT;
+            }
+            // next group: up to 32 pairs of this node
+            const unsigned g = min(32u, q1 - q);
+            bool mine = false;
+            if ((unsigned)lane < g) {
+                mine = pnode[q + lane] == node;
+            }
+            const unsigned cnt = __popc(__ballot_sync(FULL, mine));   // a prefix: pairs are node-sorted
+            if (mine) {
+                const unsigned tid = ptri[q + lane];
+                const float4* m = tri_mt + 3 * (size_t)tid;
+                float4 a = m[0];
+                a.w = __uint_as_float(tid);   // triangle id rides in the unused lane
+                s_tri[warp][lane][0] = a;
+                s_tri[warp][lane][1] = m[1];
+                s_tri[warp][lane][2] = m[2];
+            }
+            __syncwarp();
+            const unsigned nrays = min((unsigned)B, N - node * B);
+            if (lane == 0) n_tests += (unsigned long long)cnt * nrays;
+            if (rvalid) {
+                for (unsigned j = sidx; j < cnt; j += S) {
+                    float t, u, v;
+                    if (mt_test(ox, oy, oz, dx, dy, dz, tmax, s_tri[warp][j][0], s_tri[warp][j][1],
+                                s_tri[warp][j][2], t, u, v)) {
+                        ++n_hits;
+                        const unsigned long long k = hit_key(t, __float_as_uint(s_tri[warp][j][0].w));
+                        bk = k < bk ? k : bk;
+                    }
+                }
+            }
+            __syncwarp();
+            q += cnt;
+        }
+        flush();
+    }
+    n_tests = warp_sum64(n_tests);
+    n_hits = warp_sum64(n_hits);
+    if (lane == 0) {
+        if (n_tests) atomicAdd(&ctr->final_tests, n_tests);
+        if (n_hits) atomicAdd(&ctr->final_hits, n_hits);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->final_tests_paper = (unsigned long long)P * B;
+}
+
+__global__ void k_fill_best(unsigned long long* best, const unsigned* n_ptr) {
+    const unsigned n = *n_ptr;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) best[i] = NO_HIT;
+}
+
+// Moller-Trumbore in FP64 on the FP32 inputs, for the one winning triangle
+// of a ray: the FP32 test decides which triangle is closest, this pass
+// reports its (t, u, v) to FP32 rounding (FP32 alone loses digits in
+// proportion to distance / triangle size).
+__device__ __forceinline__ void mt_refine(double ox, double oy, double oz, double dx, double dy, double dz,
+                                          const crsh_scene& sc, unsigned tri, float& t, float& u, float& v) {
+    const double ax = sc.v0x[tri], ay = sc.v0y[tri], az = sc.v0z[tri];
+    const double e1x = (double)sc.v1x[tri] - ax, e1y = (double)sc.v1y[tri] - ay, e1z = (double)sc.v1z[tri] - az;
+    const double e2x = (double)sc.v2x[tri] - ax, e2y = (double)sc.v2y[tri] - ay, e2z = (double)sc.v2z[tri] - az;
+    const double px = dy * e2z - dz * e2y, py = dz * e2x - dx * e2z, pz = dx * e2y - dy * e2x;
+    const double det = e1x * px + e1y * py + e1z * pz;
+    const double inv = 1.0 / det;
+    const double sx = ox - ax, sy = oy - ay, sz = oz - az;
+    const double qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
+    u = (float)((sx * px + sy * py + sz * pz) * inv);
+    v = (float)((dx * qx + dy * qy + dz * qz) * inv);
+    t = (float)((e2x * qx + e2y * qy + e2z * qz) * inv);
+}
+
+// winner's (t, u, v) from the FP64 refinement; scatter to ray_id order
+__global__ void k_finalize(RaysDev rays, const unsigned* n_ptr, crsh_scene sc, const unsigned long long* best,
+                           crsh_hits out) {
+    const unsigned n = *n_ptr;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long k = best[i];
+        const unsigned dst = rays.ray_id[i];
+        if (k == NO_HIT) {
+            out.tri[dst] = -1;
+            out.t[dst] = out.u[dst] = out.v[dst] = 0.0f;
+            continue;
+        }
+        const unsigned tri = (unsigned)(k & 0xffffffffu);
+        float t, u, v;
+        mt_refine(rays.ox[i], rays.oy[i], rays.oz[i], rays.dx[i], rays.dy[i], rays.dz[i], sc, tri, t, u, v);
+        out.tri[dst] = (int)tri;
+        out.t[dst] = t;
+        out.u[dst] = u;
+        out.v[dst] = v;
+    }
+}
+
+// N x M: one ray per thread, triangles streamed through shared memory.
+constexpr int BF_BLOCK = 256;
+__global__ void __launch_bounds__(BF_BLOCK) k_brute(RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
+                                                    unsigned n_tris, unsigned long long* best) {
+    __shared__ float4 s_tri[BF_BLOCK][3];
+    const unsigned n = *n_ptr;
+    for (unsigned base = blockIdx.x * BF_BLOCK; base < n; base += gridDim.x * BF_BLOCK) {
+        const unsigned i = base + threadIdx.x;
+        const bool valid = i < n;
+        float ox = 0, oy = 0, oz = 0, dx = 0, dy = 0, dz = 0, tmax = 0;
+        if (valid) {
+            ox = rays.ox[i]; oy = rays.oy[i]; oz = rays.oz[i];
+            dx = rays.dx[i]; dy = rays.dy[i]; dz = rays.dz[i];
+            tmax = rays.tmax[i];
+        }
+        unsigned long long bk = NO_HIT;
+        for (unsigned t0 = 0; t0 < n_tris; t0 += BF_BLOCK) {
+            __syncthreads();
+            if (t0 + threadIdx.x < n_tris) {
+                const float4* m = tri_mt + 3 * (size_t)(t0 + threadIdx.x);
+                s_tri[threadIdx.x][0] = m[0];
+                s_tri[threadIdx.x][1] = m[1];
+                s_tri[threadIdx.x][2] = m[2];
+            }
+            __syncthreads();
+            const unsigned cnt = min((unsigned)BF_BLOCK, n_tris - t0);
+            for (unsigned j = 0; j < cnt; ++j) {
+                float t, u, v;
+                if (mt_test(ox, oy, oz, dx, dy, dz, tmax, s_tri[j][0], s_tri[j][1], s_tri[j][2], t, u, v)) {
+                    const unsigned long long k = hit_key(t, t0 + j);
+                    bk = k < bk ? k : bk;
+                }
+            }
+        }
+        if (valid) best[i] = bk;
+    }
+}
+
+size_t closest_hit_workspace(uint32_t cap) { return (size_t)cap * sizeof(unsigned long long) + 256; }
+
+static RaysDev rays_dev(const crsh_rays* r) {
+    return RaysDev{r->ox, r->oy, r->oz, r->dx, r->dy, r->dz, r->tmax, r->ray_id};
+}
+
+crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
+                               const crsh_scene* sc, const crsh_pairs* pairs, crsh_hits* out, crsh_counters* ctr,
+                               void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev) {
+    if (ws_bytes < closest_hit_workspace(rays->capacity)) return CRSH_ERR_INVALID_ARG;
+    unsigned long long* best = reinterpret_cast<unsigned long long*>(ws);
+    {
+        char* c0 = reinterpret_cast<char*>(&ctr->final_tests);
+        if (cudaMemsetAsync(c0, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) return CRSH_ERR_CUDA;
+    }
+    const unsigned fb = dev.sms * 8;
+    k_fill_best<<<fb, 256, 0, s>>>(best, n_rays);
+    const unsigned grid = dev.sms * 8;
+    const RaysDev rd = rays_dev(rays);
+    const float4* mt = reinterpret_cast<const float4*>(sc->tri_mt);
+    switch (h->bundle) {
+        case 2: k_closest<2><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
+        case 4: k_closest<4><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
+        case 8: k_closest<8><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
+        case 16: k_closest<16><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
+        case 32: k_closest<32><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
+        default: return CRSH_ERR_INVALID_ARG;
+    }
+    k_finalize<<<fb, 256, 0, s>>>(rd, n_rays, *sc, best, *out);
+    return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
+}
+
+crsh_status bruteforce_launch(const crsh_rays* rays, const uint32_t* n_rays, const crsh_scene* sc, crsh_hits* out,
+                              void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev) {
+    if (ws_bytes < closest_hit_workspace(rays->capacity)) return CRSH_ERR_INVALID_ARG;
+    unsigned long long* best = reinterpret_cast<unsigned long long*>(ws);
+    const RaysDev rd = rays_dev(rays);
+    const float4* mt = reinterpret_cast<const float4*>(sc->tri_mt);
+    const unsigned blocks = (rays->capacity + BF_BLOCK - 1) / BF_BLOCK;
+    const unsigned grid = blocks < (unsigned)dev.sms * 8 ? (blocks ? blocks : 1) : dev.sms * 8;
+    k_brute<<<grid, BF_BLOCK, 0, s>>>(rd, n_rays, mt, sc->n_tris, best);
+    k_finalize<<<dev.sms * 8, 256, 0, s>>>(rd, n_rays, *sc, best, *out);
+    return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
+}
+
+}  // namespace crsh

@@ -1,0 +1,233 @@
+"""GPU path against the CPU oracle, element by element, through the C-ABI.
+
+Sizes: config 1 (64x64, 2,050 triangles, B = 8, L = 3) and config-2 scenes at
+96x96 and 200x200 (all ray types, B = 16, L = 4: several tiles of every kernel,
+ragged last tiles and partial last nodes); config 2 at full size is in
+test_gpu_fullsize.py.  Bars: hash keys and sorted order bit-exact; hierarchy
+containment checked on the GPU's own FP32 nodes; pair counts per level within
+0.1 %; closest hits within the tolerances of tests/parity.py; GPU hierarchy
+result bit-identical to the GPU brute force."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _run(w, sort=True, compress=True, mesh_cull=True, pair_capacity=None):
+    from paper_2312_06538_gb300 import pipeline as pl
+    p = pl.workload_pipeline(w, pair_capacity=pair_capacity)
+    hp, bp = pl.workload_params(w, sort=sort, compress=compress)
+    g = p.gbuffer_to_device(w.gbuffer)
+    lights = torch.from_numpy(w.lights).cuda() if w.lights.shape[0] else None
+    c = p.run_fit(p.gbuffer_struct(g), lights, hp, bp, mesh_cull=mesh_cull)
+    return p, c
+
+
+def _oracle(w, sort=True, mesh_cull=True):
+    return oracle.run_crsh(w.gbuffer, w.lights, w.shadow_cull, w.hash_lo, w.hash_hi, w.scene, w.bundle, w.levels,
+                           w.build_pads(), sort=sort, mesh_cull=mesh_cull)
+
+
+CASES = {"c1": lambda: synthetic.make(1), "c2_96": lambda: synthetic.make(2, res=96),
+         "c2_200": lambda: synthetic.make(2, res=200)}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    w = CASES[request.param]()
+    p, c = _run(w)
+    ref = _oracle(w)
+    return w, p, c, ref
+
+
+def test_rays_keys_and_order_bit_exact(case):
+    w, p, c, ref = case
+    got = p.sorted_rays()
+    n = ref["counters"]["rays"]
+    assert c["rays"] == n and p.n() == n
+    assert c["chunks"] == ref["counters"]["chunks"]
+    assert np.array_equal(got["ray_id"], ref["perm"])
+    assert np.array_equal(got["keys"], ref["keys"][ref["perm"]])
+    sr = ref["sorted_rays"]
+    for k in oracle.RAY_FIELDS:
+        assert np.array_equal(got[k].view(np.uint32), sr[k].view(np.uint32)), k
+    assert np.array_equal(got["type"], sr["type"])
+    assert np.array_equal(got["pixel"], sr["pixel"])
+
+
+def test_hierarchy_contains_its_rays(case):
+    w, p, c, ref = case
+    lv = p.levels_host()
+    counts = [x[0].shape[0] for x in lv]
+    assert counts == oracle.level_counts(c["rays"], w.bundle, w.levels)
+    sph = np.concatenate([x[0] for x in lv])
+    con = np.concatenate([x[1] for x in lv])
+    bad, worst = oracle.check_hierarchy(ref["sorted_rays"], w.bundle, counts, sph, con)
+    assert bad == 0, (bad, worst)
+    # and close to the oracle's FP64 nodes
+    for l in range(w.levels):
+        g, r = lv[l], ref["levels"][l]
+        scale = 1.0 + np.abs(r[:, :3]).max()
+        assert np.abs(g[0][:, :3] - r[:, :3]).max() <= 1e-5 * scale
+        assert np.abs(g[0][:, 3] - r[:, 3]).max() <= 1e-4 * scale
+        open_ = r[:, 7] < np.pi / 2 - 1e-3
+        if open_.any():
+            assert np.abs(g[1][open_, 3] - r[open_, 7]).max() <= 1e-4
+
+
+def test_pair_counts_within_a_tenth_of_a_percent(case):
+    w, p, c, ref = case
+    rc = ref["counters"]
+    for l in range(w.levels):
+        assert parity.within(c["hits"][l], rc["hits"][l], 1e-3), (l, c["hits"], rc["hits"])
+        assert parity.within(c["tests"][l], rc["tests"][l], 1e-3), (l, c["tests"], rc["tests"])
+        assert parity.within(c["tests_paper"][l], rc["tests_paper"][l], 1e-3)
+    assert c["mesh_tests"] == rc["mesh_tests"]
+    assert parity.within(c["final_tests"], rc["final_tests"], 1e-3)
+    assert c["final_tests_paper"] == w.bundle * c["hits"][0]
+    for l in range(w.levels - 1):
+        assert c["tests_paper"][l] == w.bundle * c["hits"][l + 1]
+    pn, pt, off = p.pairs_host()
+    assert pn.shape[0] == c["hits"][0]
+    assert np.all(np.diff(pn.astype(np.int64)) >= 0)
+    assert off[0] == 0 and off[-1] == pn.shape[0]
+    for n in range(0, off.shape[0] - 1, max(1, (off.shape[0] - 1) // 50)):
+        seg = pt[off[n]:off[n + 1]]
+        assert np.all(pn[off[n]:off[n + 1]] == n) and np.all(np.diff(seg.astype(np.int64)) > 0)
+
+
+def test_closest_hits_match_oracle(case):
+    w, p, c, ref = case
+    gpu = p.hits_host()
+    # the oracle's hierarchy result is its brute force (pinned on the CPU); re-check a sample here
+    idx = np.random.default_rng(0).choice(c["rays"], size=min(2000, c["rays"]), replace=False)
+    sub = {k: np.ascontiguousarray(v[idx]) for k, v in ref["rays"].items()}
+    bf = oracle.bruteforce(sub, w.scene.verts)
+    assert np.array_equal(bf[0], ref["hits"][0][idx])
+    rep = parity.compare_hits(gpu, ref["hits"], ref["rays"], w.scene.verts)
+    parity.check_report(rep)
+    assert rep["hits"] > 0
+
+
+def test_hierarchy_equals_gpu_bruteforce_bitwise(case):
+    w, p, c, ref = case
+    crsh_hits = [x.copy() for x in p.hits_host()]
+    p.bruteforce()
+    bf = p.hits_host()
+    for a, b in zip(crsh_hits, bf):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_unsorted_uncompressed_and_no_mesh_cull_modes():
+    w = synthetic.make(2, res=96)
+    ref = _oracle(w, sort=False, mesh_cull=False)
+    p, c = _run(w, sort=False, mesh_cull=False)
+    got = p.sorted_rays()
+    assert np.array_equal(got["ray_id"], np.arange(c["rays"], dtype=np.uint32))
+    assert np.array_equal(got["keys"], ref["keys"])
+    top = w.levels - 1
+    assert c["tests"][top] == ref["counters"]["tests"][top] == p.levels_host()[top][0].shape[0] * w.scene.n_tris
+    assert c["mesh_tests"] == 0
+    for l in range(w.levels):
+        assert parity.within(c["hits"][l], ref["counters"]["hits"][l], 1e-3)
+    sorted_ref = _oracle(w)
+    p2, c2 = _run(w, compress=False)
+    assert np.array_equal(p2.sorted_rays()["ray_id"], sorted_ref["perm"])
+    assert c2["chunks"] == 0
+    assert np.array_equal(p.hits_host()[0], p2.hits_host()[0])
+
+
+@pytest.mark.parametrize("B,L", [(2, 3), (4, 2), (8, 5), (32, 2), (16, 1)])
+def test_bundle_and_depth(B, L):
+    import dataclasses
+    w = dataclasses.replace(synthetic.make(2, res=64), bundle=B, levels=L)
+    p, c = _run(w)
+    ref = _oracle(w)
+    for l in range(L):
+        assert parity.within(c["hits"][l], ref["counters"]["hits"][l], 1e-3)
+    rep = parity.compare_hits(p.hits_host(), ref["hits"], ref["rays"], w.scene.verts)
+    parity.check_report(rep)
+
+
+def test_empty_and_tiny_inputs():
+    from paper_2312_06538_gb300 import pipeline as pl
+    w = synthetic.make(2, res=16)
+    g = {k: v.copy() for k, v in w.gbuffer.items()}
+    g["hit"][:] = 0
+    p = pl.workload_pipeline(w)
+    hp, bp = pl.workload_params(w)
+    lights = torch.from_numpy(w.lights).cuda()
+    c = p.run_fit(p.gbuffer_struct(p.gbuffer_to_device(g)), lights, hp, bp)
+    assert c["rays"] == 0 and p.n() == 0 and c["hits"] == [0] * w.levels and c["final_tests"] == 0
+    # one glass pixel: shadow rays + reflection + refraction, down to a single partial node
+    g["hit"][137] = 1
+    g["material"][137] = synthetic.GLASS
+    c = p.run_fit(p.gbuffer_struct(p.gbuffer_to_device(g)), lights, hp, bp)
+    ref = oracle.run_crsh(g, w.lights, w.shadow_cull, w.hash_lo, w.hash_hi, w.scene, w.bundle, w.levels,
+                          w.build_pads())
+    assert c["rays"] == ref["counters"]["rays"] >= 2
+    assert np.array_equal(p.sorted_rays()["ray_id"], ref["perm"])
+    parity.check_report(parity.compare_hits(p.hits_host(), ref["hits"], ref["rays"], w.scene.verts))
+
+
+def test_capacity_overflow_is_reported_and_recovered():
+    from paper_2312_06538_gb300 import crsh as C
+    from paper_2312_06538_gb300 import pipeline as pl
+    w = synthetic.make(1)
+    p = pl.workload_pipeline(w, pair_capacity=64)
+    hp, bp = pl.workload_params(w)
+    g = p.gbuffer_struct(p.gbuffer_to_device(w.gbuffer))
+    lights = torch.from_numpy(w.lights).cuda()
+    p.run(g, lights, hp, bp)
+    c = p.read_counters()
+    assert c["status"] == C.ERR_CAPACITY and c["needed_pairs"] > 64
+    c = p.run_fit(g, lights, hp, bp)
+    assert c["status"] == C.OK and p.pair_capacity >= c["needed_pairs"]
+    ref = _oracle(w)
+    parity.check_report(parity.compare_hits(p.hits_host(), ref["hits"], ref["rays"], w.scene.verts))
+
+
+def test_ray_capacity_overflow_keeps_the_first_rays():
+    from paper_2312_06538_gb300 import crsh as C
+    from paper_2312_06538_gb300 import pipeline as pl
+    w = synthetic.make(1)
+    p = pl.Pipeline(w.scene, max_pixels=w.n_pixels, n_lights=1, bundle=w.bundle, levels=w.levels, ray_capacity=1000)
+    hp, bp = pl.workload_params(w, sort=False)
+    p.run(p.gbuffer_struct(p.gbuffer_to_device(w.gbuffer)), torch.from_numpy(w.lights).cuda(), hp, bp)
+    c = p.read_counters()
+    assert c["status"] == C.ERR_CAPACITY and c["rays"] == 4096 and p.n() == 1000
+    ref = _oracle(w, sort=False)
+    assert np.array_equal(p.sorted_rays()["keys"], ref["keys"][:1000])
+
+
+def test_prebuilt_rays_input():
+    from paper_2312_06538_gb300 import crsh as C
+    from paper_2312_06538_gb300 import pipeline as pl
+    w = synthetic.make(2, res=80)
+    ref = _oracle(w)
+    rays = ref["rays"]
+    p = pl.workload_pipeline(w)
+    hp, bp = pl.workload_params(w)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(rays[k])).cuda() for k in oracle.RAY_FIELDS + ("type", "light")}
+    n = rays["ox"].shape[0]
+    rin = p.rays_in_struct(dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(3):
+        p.hash_sort(None, None, hp, stream, rays_in=rin)
+        p.build(bp, stream)
+        p.traverse(True, stream)
+        p.closest_hit(stream)
+        c = p.read_counters()
+        if c["status"] == C.ERR_CAPACITY and c["needed_pairs"] > p.pair_capacity:
+            p.set_pair_capacity(int(1.25 * c["needed_pairs"]))
+    assert c["status"] == 0 and c["rays"] == n
+    got = p.sorted_rays()
+    assert np.array_equal(got["ray_id"], ref["perm"])
+    assert np.array_equal(got["pixel"], ref["perm"])        # input index
+    parity.check_report(parity.compare_hits(p.hits_host(), ref["hits"], ref["rays"], w.scene.verts))
