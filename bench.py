@@ -203,9 +203,9 @@ def run_reference(args, w):
 
 def launches_per_step(levels: int, compress: bool) -> int:
     """Kernels of libcrsh.so launched by one pass (count of <<<>>> in the call sequence)."""
-    hash_sort = 5 + 1 + (1 if compress else 0) + 2 + 4 + (1 if compress else 0) + 1   # tables, gen, chunk, hist+plan, 4 passes, pos, gather
+    hash_sort = 3 + 1 + (1 if compress else 0) + 2 + 4 + (1 if compress else 0) + 1   # tables, gen, chunk, hist+plan, 4 passes, pos, gather
     build = levels
-    traverse = 3 + 2 * (levels - 1) + 1
+    traverse = 1 + 4 + 5 * (levels - 1) + 1   # mesh stage, top stage, (csr + 4-kernel stage) per level, final csr
     closest = 3
     return hash_sort + build + traverse + closest
 

@@ -1,17 +1,21 @@
 // Section 3.3.7, eq. 9: top-down traversal of the sphere-cone hierarchy.
 //
-// GB300 design.  Every stage is one persistent "expand - test - compact"
-// kernel over an implicit index space whose size is read on the device:
-//   mesh stage   (top node n, mesh m)           eq. 9 against the mesh sphere
-//   top stage    (n, triangle of an accepted m) eq. 9 against the triangle sphere
-//   level stage  (pair (p, t) of the level above, child c of p), laid out
-//                child-major inside each parent's run of pairs, so the output
-//                comes out grouped by child node with triangles ascending.
-// Each tile of elements tests, ballots, scans across warps and takes its
-// output offset by decoupled look-back, then writes its pairs: one read of
-// the parent pairs, one write of the children, no flag arrays in memory.
-// A CSR offset table per level (binary search over the sorted node column)
-// lets the next level find a parent's run.
+// GB300 design.
+//   mesh stage  (top node n, mesh m): eq. 9 against the whole-mesh sphere,
+//               compacted in one pass (decoupled look-back; tiny index space).
+//   triangle stages (top level, then levels L-1 .. 1): the pairs of the stage
+//               above are the "parents".  A warp takes a chunk of 32 of a
+//               parent's triangles, loads their spheres once and tests them
+//               against every child of the parent (warp-uniform node loads),
+//               storing one ballot word per (child, chunk) in output order.
+//               A block-sum pass and an emit pass turn the ballots into
+//               (child, triangle) pairs grouped by child, triangles ascending.
+//               No per-element division, no chains of dependent loads, no
+//               waits between blocks.
+// The emit pass also records each child's run [start, end) of the output,
+// which is how the next level finds a parent's triangles.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -163,121 +167,377 @@ struct MeshOp {
     }
 };
 
-// exclusive prefix of the triangle counts of the accepted (node, mesh) pairs
-__global__ void k_mesh_scan(const uint32_t* mp_mesh, const unsigned* a_ptr, const uint32_t* mesh_first,
-                            unsigned long long* mesh_off) {
-    __shared__ unsigned long long s_w[32];
-    __shared__ unsigned long long s_carry;
-    const unsigned A = *a_ptr;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
+// ---------------------------------------------------------------------------
+// Triangle stages (top level and every lower level).
+//
+// "Parents" are the pair lists of the stage above: accepted (top node, mesh)
+// pairs for the top level, the nodes of level l+1 with their triangle runs for
+// level l.  A work unit is (parent, chunk of 32 of its triangles): one warp
+// loads the 32 triangle spheres once, tests them against every child of the
+// parent with warp-uniform node loads, and stores one 32-bit ballot per
+// (child, chunk) at its place in output order (parent, child, chunk).  A
+// block-sum pass and an emit pass then compact the ballots into (child,
+// triangle) pairs: output grouped by child, triangles ascending.
+// ---------------------------------------------------------------------------
+
+struct LevelParents {           // parents: nodes of level l+1, pair runs [start, end)
+    const uint32_t* ptri;
+    const unsigned* pstart;
+    const unsigned* pend;
+    const unsigned* n_parent;   // nodes of level l+1
+    const unsigned* n_child;    // nodes of level l
+    Node3 child;
+    unsigned logB;
+    __device__ unsigned count() const { return *n_parent; }
+    __device__ void range(unsigned p, unsigned& s, unsigned& len) const {
+        s = pstart[p];
+        len = pend[p] - s;
+    }
+    __device__ unsigned nchild(unsigned p) const {
+        const unsigned first = p << logB, cc = *n_child;
+        return first >= cc ? 0u : min(1u << logB, cc - first);
+    }
+    __device__ unsigned child_id(unsigned p, unsigned c) const { return (p << logB) + c; }
+    __device__ unsigned tri(unsigned s, unsigned j) const { return ptri[s + j]; }
+    // this parent's children own [first, last) of the output; no two parents share a child
+    __device__ bool first_of_child(unsigned, unsigned) const { return true; }
+    __device__ bool last_of_child(unsigned, unsigned) const { return true; }
+};
+
+struct TopParents {             // parents: accepted (top node, mesh) pairs, grouped by node
+    const uint32_t* mp_node;
+    const uint32_t* mp_mesh;
+    const unsigned* a_count;
+    const uint32_t* mesh_first;
+    Node3 child;                // the top level
+    __device__ unsigned count() const { return *a_count; }
+    __device__ void range(unsigned i, unsigned& s, unsigned& len) const {
+        const uint32_t m = mp_mesh[i];
+        s = mesh_first[m];
+        len = mesh_first[m + 1] - s;
+    }
+    __device__ unsigned nchild(unsigned) const { return 1u; }
+    __device__ unsigned child_id(unsigned i, unsigned) const { return mp_node[i]; }
+    __device__ unsigned tri(unsigned s, unsigned j) const { return s + j; }
+    // a top node's pairs span several mesh pairs: its run is found afterwards
+    // by k_runs_from_pairs
+    __device__ bool first_of_child(unsigned, unsigned) const { return false; }
+    __device__ bool last_of_child(unsigned, unsigned) const { return false; }
+};
+
+struct StageBuf {
+    unsigned* ubase;            // per parent: first unit        (n + 1 entries)
+    unsigned* obase;            // per parent: first ballot word (n + 1 entries)
+    unsigned* totals;           // [0] units, [1] ballot words
+    unsigned* mask;             // ballot words in output order (parent, child, chunk)
+    unsigned* pos;              // exclusive prefix of the ballot popcounts (O + 1 entries)
+    unsigned* bsum;             // per scan block: accepted pairs
+};
+
+// Pair runs of the level a stage writes: [start[n], end[n]) for node n
+// (both 0 for a node without pairs).
+struct RunOut {
+    unsigned* start;
+    unsigned* end;
+};
+
+// Single block: exclusive scans over the parents of units (chunks of 32
+// triangles) and ballot words (children x chunks); the stage's test counters.
+template <class Parents>
+__global__ void __launch_bounds__(1024) k_unit_scan(Parents par, StageBuf sb, crsh_counters* ctr, int level_idx,
+                                                    unsigned B_paper) {
+    __shared__ unsigned long long s_w[32][4];
+    __shared__ unsigned long long s_tot[4];
+    const unsigned n = par.count();
+    const unsigned per = (n + blockDim.x - 1) / blockDim.x;
+    const unsigned b0 = min(n, threadIdx.x * per), b1 = min(n, b0 + per);
+    unsigned long long u = 0, o = 0, tests = 0, paper = 0;
+    for (unsigned p = b0; p < b1; ++p) {
+        unsigned s, len;
+        par.range(p, s, len);
+        const unsigned nch = (len + 31) >> 5;
+        const unsigned nc = par.nchild(p);
+        u += nch;
+        o += (unsigned long long)nc * nch;
+        tests += (unsigned long long)nc * len;
+        paper += len;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long iu = u, io = o;
+    for (int d = 1; d < 32; d <<= 1) {
+        unsigned long long a = __shfl_up_sync(FULL, iu, d), b = __shfl_up_sync(FULL, io, d);
+        if (lane >= d) { iu += a; io += b; }
+    }
+    const unsigned long long st = warp_sum64(tests), sp = warp_sum64(paper);
+    if (lane == 31) { s_w[warp][0] = iu; s_w[warp][1] = io; }
+    if (lane == 0) { s_w[warp][2] = st; s_w[warp][3] = sp; }
     __syncthreads();
-    for (unsigned base = 0; base < A; base += blockDim.x) {
-        unsigned i = base + threadIdx.x;
-        unsigned long long v = 0;
-        if (i < A) {
-            uint32_t m = mp_mesh[i];
-            v = mesh_first[m + 1] - mesh_first[m];
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0, t = 0, q = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const unsigned long long x = s_w[w][0], y = s_w[w][1];
+            t += s_w[w][2];
+            q += s_w[w][3];
+            s_w[w][0] = a;
+            s_w[w][1] = b;
+            a += x;
+            b += y;
         }
-        unsigned long long inc = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long n = __shfl_up_sync(FULL, inc, o);
-            if (lane >= o) inc += n;
+        s_tot[0] = a; s_tot[1] = b; s_tot[2] = t; s_tot[3] = q;
+    }
+    __syncthreads();
+    unsigned long long ru = s_w[warp][0] + iu - u, ro = s_w[warp][1] + io - o;
+    for (unsigned p = b0; p < b1; ++p) {
+        unsigned s, len;
+        par.range(p, s, len);
+        const unsigned nch = (len + 31) >> 5;
+        sb.ubase[p] = (unsigned)ru;
+        sb.obase[p] = (unsigned)ro;
+        ru += nch;
+        ro += (unsigned long long)par.nchild(p) * nch;
+    }
+    if (threadIdx.x == 0) {
+        sb.ubase[n] = (unsigned)s_tot[0];
+        sb.obase[n] = (unsigned)s_tot[1];
+        sb.totals[0] = (unsigned)s_tot[0];
+        sb.totals[1] = (unsigned)s_tot[1];
+        ctr->tests[level_idx] = s_tot[2];
+        ctr->tests_paper[level_idx] = B_paper ? (unsigned long long)B_paper * s_tot[3] : s_tot[3];
+    }
+}
+
+// last p with base[p] <= u (base non-decreasing, base[0] = 0)
+__device__ __forceinline__ unsigned find_parent(const unsigned* base, unsigned n, unsigned u) {
+    unsigned lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const unsigned mid = lo + (hi - lo + 1) / 2;
+        if (base[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Walks the units [u0, u1) of a warp in order (parent by parent) and calls
+// body(p, s, len, nch, nc, ob, ch, j, valid) for each unit; warp-uniform.
+template <class Parents, class Body>
+__device__ __forceinline__ void walk_units(const Parents& par, const StageBuf& sb, unsigned u0, unsigned u1,
+                                           Body body) {
+    const int lane = threadIdx.x & 31;
+    const unsigned n = par.count();
+    unsigned p = find_parent(sb.ubase, n, u0);
+    unsigned next = sb.ubase[p + 1];
+    unsigned s, len;
+    par.range(p, s, len);
+    unsigned nch = (len + 31) >> 5, nc = par.nchild(p), ob = sb.obase[p], ub = sb.ubase[p];
+    for (unsigned u = u0; u < u1; ++u) {
+        while (u >= next) {   // parents without triangles own no units
+            ++p;
+            next = sb.ubase[p + 1];
+            par.range(p, s, len);
+            nch = (len + 31) >> 5;
+            nc = par.nchild(p);
+            ob = sb.obase[p];
+            ub = sb.ubase[p];
         }
-        if (lane == 31) s_w[warp] = inc;
-        __syncthreads();
-        unsigned long long wpre = 0;
-        for (int w = 0; w < warp; ++w) wpre += s_w[w];
-        if (i < A) mesh_off[i] = s_carry + wpre + inc - v;
+        const unsigned ch = u - ub;
+        const unsigned j = (ch << 5) + lane;
+        body(p, s, len, nch, nc, ob, ch, j, j < len);
+    }
+}
+
+__device__ __forceinline__ void warp_unit_range(unsigned U, unsigned& u0, unsigned& u1) {
+    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+    const unsigned per = (U + nw - 1) / nw;
+    u0 = min(U, gw * per);
+    u1 = min(U, u0 + per);
+}
+
+// Count pass: one 32-bit ballot per (child, chunk): eq. 9 for 32 triangles.
+template <class Parents>
+__global__ void __launch_bounds__(256) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
+    const unsigned U = sb.totals[0];
+    unsigned u0, u1;
+    warp_unit_range(U, u0, u1);
+    if (u0 >= u1) return;
+    const int lane = threadIdx.x & 31;
+    walk_units(par, sb, u0, u1,
+               [&](unsigned p, unsigned s, unsigned, unsigned nch, unsigned nc, unsigned ob, unsigned ch, unsigned j,
+                   bool valid) {
+                   float4 ts = make_float4(0.f, 0.f, 0.f, 0.f);
+                   if (valid) ts = tri_sphere[par.tri(s, j)];
+#pragma unroll 4
+                   for (unsigned c = 0; c < nc; ++c) {
+                       const unsigned a = par.child_id(p, c);
+                       const bool ok =
+                           valid && eq9(par.child.sphere[a], par.child.cone[a], par.child.trig[a], ts);
+                       const unsigned m = __ballot_sync(FULL, ok);
+                       if (lane == 0) sb.mask[ob + c * nch + ch] = m;
+                   }
+               });
+}
+
+constexpr int SC_BLOCK = 256, SC_ITEMS = 8, SC_TILE = SC_BLOCK * SC_ITEMS, SC_GRID_MAX = 2048;
+
+__device__ __forceinline__ void block_range(unsigned O, unsigned& w0, unsigned& w1) {
+    const unsigned per = (((O + gridDim.x - 1) / gridDim.x) + SC_TILE - 1) / SC_TILE * SC_TILE;
+    w0 = min(O, blockIdx.x * per);
+    w1 = min(O, w0 + per);
+}
+
+// Accepted pairs per scan block (contiguous ranges of ballot words).
+__global__ void __launch_bounds__(SC_BLOCK) k_reduce(StageBuf sb) {
+    const unsigned O = sb.totals[1];
+    unsigned w0, w1;
+    block_range(O, w0, w1);
+    unsigned c = 0;
+    for (unsigned w = w0 + threadIdx.x; w < w1; w += blockDim.x) c += __popc(sb.mask[w]);
+    c = __reduce_add_sync(FULL, c);
+    __shared__ unsigned s_w[SC_BLOCK / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int i = 0; i < SC_BLOCK / 32; ++i) t += s_w[i];
+        sb.bsum[blockIdx.x] = t;
+    }
+}
+
+// Exclusive prefix of the ballot popcounts: pos[w] = output index of the first
+// pair of word w; pos[O] = total; the stage's pair count and counters.
+__global__ void __launch_bounds__(SC_BLOCK) k_wordscan(StageBuf sb, PairOut out, crsh_counters* ctr,
+                                                       int level_idx) {
+    __shared__ unsigned long long s_pre;
+    __shared__ unsigned s_w[SC_BLOCK / 32 + 1];
+    const unsigned O = sb.totals[1];
+    unsigned w0, w1;
+    block_range(O, w0, w1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {
+        unsigned long long a = 0;
+        for (unsigned b = threadIdx.x; b < blockIdx.x; b += blockDim.x) a += sb.bsum[b];
+        a = warp_sum64(a);
+        __shared__ unsigned long long s_a[SC_BLOCK / 32];
+        if (lane == 0) s_a[warp] = a;
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long t = 0;
-            for (int w = 0; w < nw; ++w) t += s_w[w];
+            for (int i = 0; i < SC_BLOCK / 32; ++i) t += s_a[i];
+            s_pre = t;
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        const unsigned long long total = s_pre + sb.bsum[blockIdx.x];
+        sb.pos[O] = (unsigned)total;
+        finish_pairs(out, total, ctr, level_idx);
+    }
+    unsigned long long run = s_pre;
+    for (unsigned t0 = w0; t0 < w1; t0 += SC_TILE) {
+        const unsigned wb = t0 + threadIdx.x * SC_ITEMS;   // blocked: consecutive words per thread
+        unsigned c[SC_ITEMS], sum = 0;
+#pragma unroll
+        for (int i = 0; i < SC_ITEMS; ++i) {
+            c[i] = (wb + i < w1) ? __popc(sb.mask[wb + i]) : 0u;
+            sum += c[i];
+        }
+        const unsigned inc = warp_incl_scan(sum);
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned a = 0;
+            for (int i = 0; i < SC_BLOCK / 32; ++i) { const unsigned x = s_w[i]; s_w[i] = a; a += x; }
+            s_w[SC_BLOCK / 32] = a;
+        }
+        __syncthreads();
+        unsigned long long r = run + s_w[warp] + inc - sum;
+#pragma unroll
+        for (int i = 0; i < SC_ITEMS; ++i) {
+            if (wb + i < w1) sb.pos[wb + i] = (unsigned)r;
+            r += c[i];
+        }
+        run += s_w[SC_BLOCK / 32];
+        __syncthreads();
+    }
+}
+
+// Emit pass: the count pass's walk again; each set ballot bit becomes a
+// (child, triangle) pair at pos[word] + rank.  Unit (p, 0) also records the
+// children's runs [start, end).
+template <class Parents>
+__global__ void __launch_bounds__(256) k_emit(Parents par, StageBuf sb, PairOut out, RunOut runs) {
+    const unsigned U = sb.totals[0];
+    unsigned u0, u1;
+    warp_unit_range(U, u0, u1);
+    if (u0 >= u1) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    walk_units(par, sb, u0, u1,
+               [&](unsigned p, unsigned s, unsigned, unsigned nch, unsigned nc, unsigned ob, unsigned ch, unsigned j,
+                   bool valid) {
+                   const unsigned t = valid ? par.tri(s, j) : 0u;
+                   for (unsigned c = 0; c < nc; ++c) {
+                       const unsigned w = ob + c * nch + ch;
+                       const unsigned m = sb.mask[w];
+                       if ((m >> lane) & 1u) store_pair(out, sb.pos[w] + __popc(m & lt), par.child_id(p, c), t);
+                   }
+                   if (ch == 0 && (unsigned)lane < nc) {
+                       // runs index the written list: clamp to its capacity (a list
+                       // that overflowed is truncated and flagged CRSH_ERR_CAPACITY)
+                       const unsigned c = lane, a = par.child_id(p, c);
+                       if (par.first_of_child(p, c))
+                           runs.start[a] = (unsigned)min((unsigned long long)sb.pos[ob + c * nch], out.cap);
+                       if (par.last_of_child(p, c))
+                           runs.end[a] = (unsigned)min((unsigned long long)sb.pos[ob + (c + 1) * nch], out.cap);
+                   }
+               });
+}
+
+// Runs of a node-sorted pair list by binary search (the top level: few nodes).
+__global__ void k_runs_from_pairs(const uint32_t* node, const unsigned* p_count, const unsigned* n_count,
+                                  RunOut runs) {
+    const unsigned P = *p_count, Nn = *n_count;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < Nn; k += gridDim.x * blockDim.x) {
+        unsigned b[2];
+        for (int e = 0; e < 2; ++e) {
+            unsigned lo = 0, hi = P;
+            while (lo < hi) {
+                const unsigned mid = (lo + hi) >> 1;
+                if (node[mid] < k + e) lo = mid + 1; else hi = mid;
+            }
+            b[e] = lo;
+        }
+        runs.start[k] = b[0];
+        runs.end[k] = b[1];
+    }
+}
+
+// CSR offsets (n + 1) from the pair runs of a level: off[k] = pairs of nodes
+// before k (single block).
+__global__ void __launch_bounds__(1024) k_runs_to_csr(RunOut runs, const unsigned* n_count, uint32_t* off) {
+    __shared__ unsigned s_w[32];
+    __shared__ unsigned s_carry;
+    const unsigned n = *n_count;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (unsigned base = 0; base < n; base += blockDim.x) {
+        const unsigned k = base + threadIdx.x;
+        const unsigned v = k < n ? runs.end[k] - runs.start[k] : 0u;
+        const unsigned inc = warp_incl_scan(v);
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        unsigned wpre = 0;
+        for (int i = 0; i < warp; ++i) wpre += s_w[i];
+        if (k < n) off[k] = s_carry + wpre + inc - v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned t = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_w[i];
             s_carry += t;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) mesh_off[A] = s_carry;
-}
-
-// ---- top stage: (top node, triangle of an accepted mesh) -----------------
-struct TopOp {
-    Node3 top;
-    const uint32_t* mp_node;
-    const uint32_t* mp_mesh;
-    const unsigned* a_ptr;
-    const unsigned long long* mesh_off;
-    const uint32_t* mesh_first;
-    const float4* tri_sphere;
-    PairOut out;
-    crsh_counters* ctr;
-    int level_idx;
-    __device__ unsigned long long size() const { return mesh_off[*a_ptr]; }
-    __device__ bool test(unsigned long long e, uint32_t& a, uint32_t& b, bool& valid) const {
-        const unsigned A = *a_ptr;
-        unsigned lo = 0, hi = A - 1;   // last i with mesh_off[i] <= e
-        while (lo < hi) {
-            unsigned mid = lo + (hi - lo + 1) / 2;
-            if (mesh_off[mid] <= e) lo = mid; else hi = mid - 1;
-        }
-        a = mp_node[lo];
-        b = mesh_first[mp_mesh[lo]] + (uint32_t)(e - mesh_off[lo]);
-        valid = true;
-        return eq9(top.sphere[a], top.cone[a], top.trig[a], tri_sphere[b]);
-    }
-    __device__ void emit(unsigned long long pos, uint32_t a, uint32_t b) const { store_pair(out, pos, a, b); }
-    __device__ void finish(unsigned long long total) const {
-        finish_pairs(out, total, ctr, level_idx);
-        ctr->tests_paper[level_idx] = mesh_off[*a_ptr];
-    }
-};
-
-// ---- level stage: (pair (p, t) of level l+1, child c of p) ---------------
-struct LevelOp {
-    Node3 child;
-    const unsigned* child_count;
-    const uint32_t* pnode;     // parent pairs, grouped by parent
-    const uint32_t* ptri;
-    const unsigned* p_count;
-    const uint32_t* poff;      // CSR of the parent level
-    unsigned logB;
-    const float4* tri_sphere;
-    PairOut out;
-    crsh_counters* ctr;
-    int level_idx;
-    __device__ unsigned long long size() const { return (unsigned long long)(*p_count) << logB; }
-    __device__ bool test(unsigned long long e, uint32_t& a, uint32_t& b, bool& valid) const {
-        const unsigned j = (unsigned)(e >> logB);
-        const uint32_t p = pnode[j];
-        const uint32_t s = poff[p];
-        const uint32_t len = poff[p + 1] - s;
-        const uint32_t o = (uint32_t)(e - ((unsigned long long)s << logB));   // < B * len
-        const uint32_t c = o / len;
-        const uint32_t k = o - c * len;
-        a = (p << logB) + c;
-        if (a >= *child_count) return false;   // padded slot of a partial last node
-        b = ptri[s + k];
-        valid = true;
-        return eq9(child.sphere[a], child.cone[a], child.trig[a], tri_sphere[b]);
-    }
-    __device__ void emit(unsigned long long pos, uint32_t a, uint32_t b) const { store_pair(out, pos, a, b); }
-    __device__ void finish(unsigned long long total) const {
-        finish_pairs(out, total, ctr, level_idx);
-        ctr->tests_paper[level_idx] = (unsigned long long)(*p_count) << logB;
-    }
-};
-
-// CSR offsets over a node-sorted pair list: off[n] = first pair of node n.
-__global__ void k_csr(const uint32_t* node, const unsigned* p_count, const unsigned* n_count, uint32_t* off) {
-    const unsigned P = *p_count, Nn = *n_count;
-    for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n <= Nn; n += gridDim.x * blockDim.x) {
-        unsigned lo = 0, hi = P;
-        while (lo < hi) {
-            unsigned mid = (lo + hi) >> 1;
-            if (node[mid] < n) lo = mid + 1; else hi = mid;
-        }
-        off[n] = lo;
-    }
+    if (threadIdx.x == 0) off[n] = s_carry;
 }
 
 // ---------------------------------------------------------------------------
@@ -299,13 +559,13 @@ struct Carve {
 struct TvWs {
     uint32_t *bufN[2], *bufT[2];         // ping-pong pair lists of the levels above 1
     uint32_t *mpN, *mpM;                 // accepted (node, mesh)
-    unsigned long long* mesh_off;
-    uint32_t* off[CRSH_MAX_LEVELS];      // CSR per level >= 2
-    char* ctl;
+    RunOut runs[CRSH_MAX_LEVELS];        // pair runs per level
+    StageBuf sb;
+    char* ctl;                           // zeroed per call: counts, counters, runs
     size_t ctl_bytes;
     unsigned* counts;                    // [0] mesh pairs, [1 + l] pairs of level l+1
-    unsigned* tile_ctr;                  // one per stage
-    unsigned long long* st[CRSH_MAX_LEVELS + 2];
+    unsigned* tile_ctr;
+    unsigned long long* st_mesh;
     size_t total;
 };
 
@@ -323,15 +583,26 @@ TvWs carve_tv(void* ws, const crsh_hierarchy* h, uint32_t n_tris, uint32_t n_mes
     }
     w.mpN = c.take<uint32_t>(mp);
     w.mpM = c.take<uint32_t>(mp);
-    w.mesh_off = c.take<unsigned long long>(mp + 1);
-    for (unsigned l = 1; l < L; ++l) w.off[l] = c.take<uint32_t>((size_t)h->capacity[l] + 1);
+    size_t max_parents = mp, max_words = (size_t)(top_cap * (uint64_t)n_tris / 32) + mp;
+    for (unsigned l = 1; l < L; ++l) {
+        max_parents = std::max(max_parents, (size_t)h->capacity[l]);
+        max_words = std::max(max_words, (size_t)B * ((size_t)(cap / 32) + h->capacity[l]));
+    }
+    w.sb.ubase = c.take<unsigned>(max_parents + 1);
+    w.sb.obase = c.take<unsigned>(max_parents + 1);
+    w.sb.totals = c.take<unsigned>(4);
+    w.sb.mask = c.take<unsigned>(max_words + 1);
+    w.sb.pos = c.take<unsigned>(max_words + 1);
+    w.sb.bsum = c.take<unsigned>(SC_GRID_MAX);
     c.off = (c.off + 255) & ~size_t(255);
     const size_t ctl0 = c.off;
     w.counts = c.take<unsigned>(CRSH_MAX_LEVELS + 2);
-    w.tile_ctr = c.take<unsigned>(CRSH_MAX_LEVELS + 2);
-    w.st[0] = c.take<unsigned long long>(mp / TV_TILE + 2);                                  // mesh stage
-    w.st[1] = c.take<unsigned long long>((size_t)(top_cap * (uint64_t)n_tris / TV_TILE) + 2); // top stage
-    for (unsigned l = 2; l < L + 1; ++l) w.st[l] = c.take<unsigned long long>((size_t)(cap * B / TV_TILE) + 2);
+    w.tile_ctr = c.take<unsigned>(4);
+    w.st_mesh = c.take<unsigned long long>(mp / TV_TILE + 2);
+    for (unsigned l = 0; l < L; ++l) {
+        w.runs[l].start = c.take<unsigned>((size_t)h->capacity[l] + 1);
+        w.runs[l].end = c.take<unsigned>((size_t)h->capacity[l] + 1);
+    }
     w.ctl = ws ? reinterpret_cast<char*>(ws) + ctl0 : nullptr;
     w.ctl_bytes = c.off - ctl0;
     w.total = c.off + 256;
@@ -349,9 +620,16 @@ size_t traverse_workspace(const crsh_hierarchy* h, uint32_t n_tris, uint32_t n_m
     return carve_tv(nullptr, h, n_tris, n_meshes, cap).total;
 }
 
-template <class Op>
-static void launch_compact(const Op& op, TvCtl ctl, unsigned grid, cudaStream_t s) {
-    k_compact<Op><<<grid, TV_BLOCK, 0, s>>>(op, ctl);
+template <class Parents>
+static void run_stage(const Parents& par, const TvWs& w, const float4* tsph, PairOut out, RunOut runs,
+                      crsh_counters* ctr, int level_idx, unsigned B_paper, const DeviceInfo& dev, cudaStream_t s) {
+    const unsigned warps_grid = dev.sms * 8;   // 256-thread blocks
+    const unsigned sg = std::min<unsigned>(SC_GRID_MAX, dev.sms * 2);
+    k_unit_scan<Parents><<<1, 1024, 0, s>>>(par, w.sb, ctr, level_idx, B_paper);
+    k_count<Parents><<<warps_grid, 256, 0, s>>>(par, w.sb, tsph);
+    k_reduce<<<sg, SC_BLOCK, 0, s>>>(w.sb);
+    k_wordscan<<<sg, SC_BLOCK, 0, s>>>(w.sb, out, ctr, level_idx);
+    k_emit<Parents><<<warps_grid, 256, 0, s>>>(par, w.sb, out, runs);
 }
 
 crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const crsh_traverse_params* tp,
@@ -362,51 +640,43 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     if (ws_bytes < traverse_workspace(h, sc->n_tris, sc->n_meshes, cap)) return CRSH_ERR_INVALID_ARG;
     TvWs w = carve_tv(ws, h, sc->n_tris, sc->n_meshes, cap);
     if (cudaMemsetAsync(w.ctl, 0, w.ctl_bytes, s) != cudaSuccess) return CRSH_ERR_CUDA;
-    // reset this call's counters: mesh_tests .. needed_pairs
-    {
+    {   // reset this call's counters: mesh_tests .. tests_paper, and needed_pairs
         char* c0 = reinterpret_cast<char*>(&ctr->mesh_tests);
         char* c1 = reinterpret_cast<char*>(&ctr->final_tests);
         if (cudaMemsetAsync(c0, 0, (size_t)(c1 - c0), s) != cudaSuccess) return CRSH_ERR_CUDA;
         if (cudaMemsetAsync(&ctr->needed_pairs, 0, sizeof(unsigned long long), s) != cudaSuccess) return CRSH_ERR_CUDA;
     }
-    const unsigned grid = dev.sms * 4;
     auto level_nodes = [&](unsigned l) {   // l = 1..L
         return Node3{reinterpret_cast<const float4*>(h->sphere[l - 1]), reinterpret_cast<const float4*>(h->cone[l - 1]),
                      reinterpret_cast<const float2*>(h->trig[l - 1])};
     };
     const float4* tsph = reinterpret_cast<const float4*>(sc->tri_sphere);
-    // pair list of level l: level 1 -> out; others ping-pong in the workspace
     auto pairs_of = [&](unsigned l) {
         if (l == 1) return PairOut{out->node, out->tri, out->count, cap};
         return PairOut{w.bufN[l & 1], w.bufT[l & 1], &w.counts[1 + l], cap};
     };
-
-    // mesh stage
+    // mesh stage: (top node, mesh)
     MeshOp mop{level_nodes(L), h->count + (L - 1), reinterpret_cast<const float4*>(sc->mesh_sphere),
                sc->mesh_first_tri, sc->n_meshes, (int)tp->mesh_cull,
                PairOut{w.mpN, w.mpM, &w.counts[0], (unsigned long long)h->capacity[L - 1] * sc->n_meshes}, ctr};
-    launch_compact(mop, TvCtl{w.st[0], &w.tile_ctr[0], ctr, -1}, grid, s);
-    k_mesh_scan<<<1, 1024, 0, s>>>(w.mpM, &w.counts[0], sc->mesh_first_tri, w.mesh_off);
-    // top stage
-    TopOp top{level_nodes(L), w.mpN, w.mpM, &w.counts[0], w.mesh_off, sc->mesh_first_tri, tsph, pairs_of(L), ctr,
-              (int)L - 1};
-    launch_compact(top, TvCtl{w.st[1], &w.tile_ctr[1], ctr, (int)L - 1}, grid, s);
-    // lower levels
+    k_compact<MeshOp><<<dev.sms * 2, TV_BLOCK, 0, s>>>(mop, TvCtl{w.st_mesh, &w.tile_ctr[0], ctr, -1});
+    // top level: triangles of the accepted meshes
+    TopParents top{w.mpN, w.mpM, &w.counts[0], sc->mesh_first_tri, level_nodes(L)};
+    run_stage(top, w, tsph, pairs_of(L), w.runs[L - 1], ctr, (int)L - 1, 0u, dev, s);
+    {
+        const PairOut tp_out = pairs_of(L);
+        const unsigned blocks = (h->capacity[L - 1] + 255) / 256;
+        k_runs_from_pairs<<<std::min<unsigned>(blocks, dev.sms * 4), 256, 0, s>>>(tp_out.node, tp_out.count,
+                                                                                  h->count + (L - 1), w.runs[L - 1]);
+    }
+    // levels L-1 .. 1: parents are the nodes of level l+1 and their pair runs
     for (unsigned l = L - 1; l >= 1; --l) {
         PairOut par = pairs_of(l + 1);
-        uint32_t* poff = w.off[l];   // CSR of level l+1 (index l = level l+1 - 1)
-        const unsigned csr_blocks = (h->capacity[l] + 1 + 255) / 256;
-        k_csr<<<csr_blocks < (unsigned)grid ? csr_blocks : grid, 256, 0, s>>>(par.node, par.count, h->count + l, poff);
-        LevelOp op{level_nodes(l), h->count + (l - 1), par.node, par.tri, par.count, poff, logB, tsph, pairs_of(l), ctr,
-                   (int)l - 1};
-        launch_compact(op, TvCtl{w.st[l + 1], &w.tile_ctr[l + 1], ctr, (int)l - 1}, grid, s);
+        LevelParents lp{par.tri, w.runs[l].start, w.runs[l].end, h->count + l, h->count + (l - 1), level_nodes(l), logB};
+        run_stage(lp, w, tsph, pairs_of(l), w.runs[l - 1], ctr, (int)l - 1, B, dev, s);
         if (l == 1) break;
     }
-    {
-        const unsigned csr_blocks = (h->capacity[0] + 1 + 255) / 256;
-        k_csr<<<csr_blocks < (unsigned)grid ? csr_blocks : grid, 256, 0, s>>>(out->node, out->count, h->count,
-                                                                               out->node_offsets);
-    }
+    k_runs_to_csr<<<1, 1024, 0, s>>>(w.runs[0], h->count, out->node_offsets);
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
 }
 
