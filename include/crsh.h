@@ -249,6 +249,27 @@ crsh_status crsh_closest_hit(const crsh_hierarchy *h, const crsh_rays *rays, con
                              crsh_counters *counters, void *workspace, size_t workspace_bytes,
                              void *stream);
 
+/* crsh_closest_hit without a caller-supplied workspace.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory - code that runs while a CUDA graph is being captured (where
+ * cudaMalloc is not allowed), real-time loops that must never reach the
+ * allocator (cudaMalloc can synchronise the whole device), or plugins inside
+ * a host application whose allocator owns all device memory.
+ * The per-ray scratch (8 bytes per ray) is a fixed array inside the library
+ * sized for CRSH_NOALLOC_MAX_RAYS rays (16 MiB); every GPU that loads the
+ * library holds it until the process exits.  rays->capacity above
+ * CRSH_NOALLOC_MAX_RAYS is rejected with CRSH_ERR_INVALID_ARG before anything
+ * is launched.  The first call on each device looks up the array's device
+ * address, so make that first call before any stream capture.  All calls
+ * share the one array (each call resets the part it uses): calls that may
+ * overlap on the GPU - other streams or other host threads on the same
+ * device - race and must be serialised by the caller.  Arguments and results
+ * are those of crsh_closest_hit. */
+#define CRSH_NOALLOC_MAX_RAYS (1u << 21)
+crsh_status crsh_closest_hit_noalloc(const crsh_hierarchy *h, const crsh_rays *rays, const uint32_t *n_rays,
+                                     const crsh_scene *scene, const crsh_pairs *pairs, crsh_hits *out,
+                                     crsh_counters *counters, void *stream);
+
 /* Every ray against every triangle with the same test (Section 1's N x M
  * baseline); results bit-identical to crsh_closest_hit when culling is
  * conservative. */

@@ -94,6 +94,9 @@ SIGNATURES = [
     ("crsh_closest_hit", ctypes.c_int,
      [ctypes.POINTER(crsh_hierarchy), ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_scene),
       ctypes.POINTER(crsh_pairs), ctypes.POINTER(crsh_hits), P, P, ctypes.c_size_t, P]),
+    ("crsh_closest_hit_noalloc", ctypes.c_int,
+     [ctypes.POINTER(crsh_hierarchy), ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_scene),
+      ctypes.POINTER(crsh_pairs), ctypes.POINTER(crsh_hits), P, P]),
     ("crsh_bruteforce_closest_hit", ctypes.c_int,
      [ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_scene), ctypes.POINTER(crsh_hits), P, ctypes.c_size_t, P]),
 ]
@@ -186,3 +189,14 @@ def crsh_bruteforce_closest_hit(rays: crsh_rays, n_rays: int, scene: crsh_scene,
     _check("crsh_bruteforce_closest_hit",
            load().crsh_bruteforce_closest_hit(ctypes.byref(rays), P(n_rays), ctypes.byref(scene), ctypes.byref(out),
                                               P(workspace), workspace_bytes, P(stream)))
+
+
+NOALLOC_MAX_RAYS = 1 << 21
+
+
+def crsh_closest_hit_noalloc(h: crsh_hierarchy, rays: crsh_rays, n_rays: int, scene: crsh_scene, pairs: crsh_pairs,
+                             out: crsh_hits, counters: int, stream: int):
+    """crsh_closest_hit with the library's own fixed scratch (for callers that cannot allocate)."""
+    _check("crsh_closest_hit_noalloc",
+           load().crsh_closest_hit_noalloc(ctypes.byref(h), ctypes.byref(rays), P(n_rays), ctypes.byref(scene),
+                                           ctypes.byref(pairs), ctypes.byref(out), P(counters), P(stream)))

@@ -163,6 +163,19 @@ crsh_status crsh_closest_hit(const crsh_hierarchy* h, const crsh_rays* rays, con
                               static_cast<cudaStream_t>(stream), dev);
 }
 
+crsh_status crsh_closest_hit_noalloc(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
+                                     const crsh_scene* scene, const crsh_pairs* pairs, crsh_hits* out,
+                                     crsh_counters* counters, void* stream) {
+    if (!hier_ok(h) || !rays_ok(rays) || !n_rays || !scene_ok(scene, true) || !pairs || !pairs->node ||
+        !pairs->tri || !pairs->count || !out || !out->tri || !out->t || !out->u || !out->v || !counters)
+        return CRSH_ERR_INVALID_ARG;
+    if (rays->capacity > CRSH_NOALLOC_MAX_RAYS) return CRSH_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if (!current_device(dev)) return CRSH_ERR_CUDA;
+    return closest_hit_noalloc_launch(h, rays, n_rays, scene, pairs, out, counters,
+                                      static_cast<cudaStream_t>(stream), dev);
+}
+
 crsh_status crsh_bruteforce_closest_hit(const crsh_rays* rays, const uint32_t* n_rays, const crsh_scene* scene,
                                         crsh_hits* out, void* workspace, size_t workspace_bytes, void* stream) {
     if (!rays_ok(rays) || !n_rays || !scene_ok(scene, true) || !out || !out->tri || !out->t || !out->u || !out->v ||

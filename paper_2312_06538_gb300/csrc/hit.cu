@@ -14,6 +14,8 @@
 // of the winning triangle with the same test and scatters hits to the rays'
 // generation order.  Decisions (which triangle is closest) are FP32; the
 // reported (t, u, v) of the winner are recomputed in FP64 from the FP32 inputs.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -266,6 +268,39 @@ crsh_status bruteforce_launch(const crsh_rays* rays, const uint32_t* n_rays, con
     k_brute<<<grid, BF_BLOCK, 0, s>>>(rd, n_rays, mt, sc->n_tris, best);
     k_finalize<<<dev.sms * 8, 256, 0, s>>>(rd, n_rays, *sc, best, *out);
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free closest hit.  The per-ray scratch that crsh_closest_hit
+// takes from the caller's workspace (one 64-bit key per ray) lives here in a
+// fixed device array instead, so a caller that cannot allocate device memory
+// passes only inputs and outputs.  Every GPU that loads the library holds the
+// array until the process exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned long long g_noalloc_best[CRSH_NOALLOC_MAX_RAYS + 32];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[64];
+
+crsh_status closest_hit_noalloc_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
+                                       const crsh_scene* sc, const crsh_pairs* pairs, crsh_hits* out,
+                                       crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev) {
+    if (rays->capacity > CRSH_NOALLOC_MAX_RAYS) return CRSH_ERR_INVALID_ARG;
+    if (dev.device < 0 || dev.device >= 64) return CRSH_ERR_CUDA;
+    void* scratch = nullptr;
+    {
+        // Host code only knows the array by its host-side stand-in: look up
+        // its device address once per device, with that device current.
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev.device]) {
+            void* a = nullptr;
+            if (cudaGetSymbolAddress(&a, g_noalloc_best) != cudaSuccess || !a) return CRSH_ERR_CUDA;
+            g_noalloc_addr[dev.device] = a;
+        }
+        scratch = g_noalloc_addr[dev.device];
+    }
+    // the existing path; it re-initialises every key it reads (no-hit) first
+    return closest_hit_launch(h, rays, n_rays, sc, pairs, out, ctr, scratch, sizeof(g_noalloc_best), s, dev);
 }
 
 }  // namespace crsh

@@ -41,6 +41,9 @@ size_t closest_hit_workspace(uint32_t ray_capacity);
 crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
                                const crsh_scene* sc, const crsh_pairs* pairs, crsh_hits* out, crsh_counters* ctr,
                                void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev);
+crsh_status closest_hit_noalloc_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
+                                       const crsh_scene* sc, const crsh_pairs* pairs, crsh_hits* out,
+                                       crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev);
 crsh_status bruteforce_launch(const crsh_rays* rays, const uint32_t* n_rays, const crsh_scene* sc, crsh_hits* out,
                               void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev);
 
