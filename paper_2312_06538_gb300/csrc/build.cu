@@ -229,8 +229,8 @@ crsh_status build_launch(const crsh_rays* rays, const uint32_t* n_rays, const cr
 
 // ---------------------------------------------------------------------------
 // Scene preparation: triangle spheres (centroid, largest vertex distance,
-// padded outward by a few FP32 ulps of the coordinates) and the
-// (v0, v1 - v0, v2 - v0) layout read by the final tests.
+// padded outward by a few FP32 ulps of the coordinates) and the record read
+// by the final tests: v0, e1 = v1 - v0, e2 = v2 - v0 and n = e1 x e2.
 // ---------------------------------------------------------------------------
 __global__ void k_prepare(crsh_scene sc) {
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < sc.n_tris; t += gridDim.x * blockDim.x) {
@@ -243,10 +243,11 @@ __global__ void k_prepare(crsh_scene sc) {
         r = r * (1.0f + 9.6e-7f) + 3.9e-6f * mag;   // covers the FP32 error of eq. 9 at this distance
         reinterpret_cast<float4*>(sc.tri_sphere)[t] = make_float4(m.x, m.y, m.z, r);
         f3 e1 = b - a, e2 = c - a;
+        f3 n = cross(e1, e2);
         float4* mt = reinterpret_cast<float4*>(sc.tri_mt) + 3 * (size_t)t;
-        mt[0] = make_float4(a.x, a.y, a.z, 0.0f);
-        mt[1] = make_float4(e1.x, e1.y, e1.z, 0.0f);
-        mt[2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+        mt[0] = make_float4(a.x, a.y, a.z, n.x);
+        mt[1] = make_float4(e1.x, e1.y, e1.z, n.y);
+        mt[2] = make_float4(e2.x, e2.y, e2.z, n.z);
     }
 }
 

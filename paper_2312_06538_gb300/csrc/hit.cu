@@ -23,23 +23,33 @@ namespace crsh {
 
 // Moller-Trumbore in FP32 with an explicit operation sequence (fused
 // multiply-adds written out), so every kernel that calls it gets the same
-// bits.  Two-sided; a zero determinant fails every range test below through
-// the infinite reciprocal; inclusive edges; 0 < t <= t_max.
-__device__ __forceinline__ bool mt_test(float ox, float oy, float oz, float dx, float dy, float dz, float tmax,
-                                        float4 a, float4 e1, float4 e2, float& t, float& u, float& v) {
-    const float px = __fmaf_rn(dy, e2.z, __fmul_rn(-dz, e2.y));
-    const float py = __fmaf_rn(dz, e2.x, __fmul_rn(-dx, e2.z));
-    const float pz = __fmaf_rn(dx, e2.y, __fmul_rn(-dy, e2.x));
-    const float det = __fmaf_rn(e1.x, px, __fmaf_rn(e1.y, py, __fmul_rn(e1.z, pz)));
-    const float inv = __frcp_rn(det);
-    const float sx = __fsub_rn(ox, a.x), sy = __fsub_rn(oy, a.y), sz = __fsub_rn(oz, a.z);
-    u = __fmul_rn(__fmaf_rn(sx, px, __fmaf_rn(sy, py, __fmul_rn(sz, pz))), inv);
-    const float qx = __fmaf_rn(sy, e1.z, __fmul_rn(-sz, e1.y));
-    const float qy = __fmaf_rn(sz, e1.x, __fmul_rn(-sx, e1.z));
-    const float qz = __fmaf_rn(sx, e1.y, __fmul_rn(-sy, e1.x));
-    v = __fmul_rn(__fmaf_rn(dx, qx, __fmaf_rn(dy, qy, __fmul_rn(dz, qz))), inv);
-    t = __fmul_rn(__fmaf_rn(e2.x, qx, __fmaf_rn(e2.y, qy, __fmul_rn(e2.z, qz))), inv);
-    return (u >= 0.0f) & (v >= 0.0f) & (__fadd_rn(u, v) <= 1.0f) & (t > 0.0f) & (t <= tmax);
+// bits.  Cramer's rule for o + t d = a + u e1 + v e2 with the triangle normal
+// n = e1 x e2 precomputed: D = -(d.n), t = (s.n)/D, u = (e2.q)/D,
+// v = -(e1.q)/D with s = o - a and q = s x d (21 FP32 operations).  The
+// numerators are compared against |D| after folding D's sign into them, so no
+// reciprocal is needed; the one division t = t'/|D| happens only on a hit.
+// Two-sided, inclusive edges, 0 < t <= t_max, D == 0 never hits.
+// Triangle record: (a.xyz, n.x), (e1.xyz, n.y), (e2.xyz, n.z).
+__device__ __forceinline__ bool mt_hit(float ox, float oy, float oz, float dx, float dy, float dz, float tmax,
+                                       float4 A, float4 E1, float4 E2, float& t) {
+    const float dn = __fmaf_rn(dx, A.w, __fmaf_rn(dy, E1.w, __fmul_rn(dz, E2.w)));   // d.n = -D
+    const float sx = __fsub_rn(ox, A.x), sy = __fsub_rn(oy, A.y), sz = __fsub_rn(oz, A.z);
+    const float qx = __fmaf_rn(sy, dz, __fmul_rn(-sz, dy));
+    const float qy = __fmaf_rn(sz, dx, __fmul_rn(-sx, dz));
+    const float qz = __fmaf_rn(sx, dy, __fmul_rn(-sy, dx));
+    const float tn = __fmaf_rn(sx, A.w, __fmaf_rn(sy, E1.w, __fmul_rn(sz, E2.w)));     // s.n
+    const float un = __fmaf_rn(E2.x, qx, __fmaf_rn(E2.y, qy, __fmul_rn(E2.z, qz)));    // e2.q
+    const float wn = __fmaf_rn(E1.x, qx, __fmaf_rn(E1.y, qy, __fmul_rn(E1.z, qz)));    // e1.q = -v D
+    // sign of D = -dn: fold it into t' = s.n, u' = e2.q and v' = -(e1.q)
+    const unsigned sgD = (__float_as_uint(dn) & 0x80000000u) ^ 0x80000000u;
+    const float u = __uint_as_float(__float_as_uint(un) ^ sgD);
+    const float v = __uint_as_float(__float_as_uint(wn) ^ sgD ^ 0x80000000u);
+    const float tp = __uint_as_float(__float_as_uint(tn) ^ sgD);
+    const float ad = fabsf(dn);
+    const bool hit = (u >= 0.0f) & (v >= 0.0f) & (__fadd_rn(u, v) <= ad) & (tp > 0.0f) & (ad > 0.0f) &
+                     (tp <= __fmul_rn(tmax, ad));
+    if (hit) t = __fdiv_rn(tp, ad);
+    return hit && t > 0.0f && t <= tmax;
 }
 
 __device__ __forceinline__ unsigned long long hit_key(float t, unsigned tri) {
@@ -54,6 +64,18 @@ struct RaysDev {
 
 constexpr int CH_WARPS = 4, CH_BLOCK = CH_WARPS * 32, CH_CHUNK = 512;
 
+// min over the 32/B lanes that hold the same ray, then one atomicMin per ray
+template <int B>
+__device__ __forceinline__ void flush_best(unsigned long long bk, bool rvalid, int sidx, unsigned ray,
+                                           unsigned long long* best) {
+#pragma unroll
+    for (int o = B; o < 32; o <<= 1) {
+        const unsigned long long other = __shfl_xor_sync(FULL, bk, o);
+        bk = other < bk ? other : bk;
+    }
+    if (rvalid && sidx == 0 && bk != NO_HIT) atomicMin(&best[ray], bk);
+}
+
 template <int B>
 __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, const uint32_t* ptri,
                                                       const unsigned* p_count, unsigned long long p_cap,
@@ -61,6 +83,7 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
                                                       unsigned long long* best, crsh_counters* ctr) {
     constexpr int S = 32 / B;
     __shared__ float4 s_tri[CH_WARPS][32][3];
+    __shared__ unsigned s_tid[CH_WARPS][32];
     const unsigned P = (unsigned)min((unsigned long long)*p_count, p_cap);
     const unsigned N = *n_ptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -73,20 +96,11 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
         bool rvalid = false;
         float ox = 0, oy = 0, oz = 0, dx = 0, dy = 0, dz = 0, tmax = 0;
         unsigned long long bk = NO_HIT;
-        auto flush = [&]() {
-            unsigned long long k = bk;
-#pragma unroll
-            for (int o = B; o < 32; o <<= 1) {
-                unsigned long long other = __shfl_xor_sync(FULL, k, o);
-                k = other < k ? other : k;
-            }
-            if (rvalid && sidx == 0 && k != NO_HIT) atomicMin(&best[ray], k);
-        };
         unsigned q = q0;
         while (q < q1) {
             const unsigned node = pnode[q];   // same address in every lane
             if (node != cur) {
-                flush();
+                flush_best<B>(bk, rvalid, sidx, ray, best);
                 cur = node;
                 ray = node * B + r;
                 rvalid = ray < N;
@@ -107,9 +121,8 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
             if (mine) {
                 const unsigned tid = ptri[q + lane];
                 const float4* m = tri_mt + 3 * (size_t)tid;
-                float4 a = m[0];
-                a.w = __uint_as_float(tid);   // triangle id rides in the unused lane
-                s_tri[warp][lane][0] = a;
+                s_tid[warp][lane] = tid;
+                s_tri[warp][lane][0] = m[0];
                 s_tri[warp][lane][1] = m[1];
                 s_tri[warp][lane][2] = m[2];
             }
@@ -118,11 +131,11 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
             if (lane == 0) n_tests += (unsigned long long)cnt * nrays;
             if (rvalid) {
                 for (unsigned j = sidx; j < cnt; j += S) {
-                    float t, u, v;
-                    if (mt_test(ox, oy, oz, dx, dy, dz, tmax, s_tri[warp][j][0], s_tri[warp][j][1],
-                                s_tri[warp][j][2], t, u, v)) {
+                    float t;
+                    if (mt_hit(ox, oy, oz, dx, dy, dz, tmax, s_tri[warp][j][0], s_tri[warp][j][1],
+                               s_tri[warp][j][2], t)) {
                         ++n_hits;
-                        const unsigned long long k = hit_key(t, __float_as_uint(s_tri[warp][j][0].w));
+                        const unsigned long long k = hit_key(t, s_tid[warp][j]);
                         bk = k < bk ? k : bk;
                     }
                 }
@@ -130,7 +143,7 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
             __syncwarp();
             q += cnt;
         }
-        flush();
+        flush_best<B>(bk, rvalid, sidx, ray, best);
     }
     n_tests = warp_sum64(n_tests);
     n_hits = warp_sum64(n_hits);
@@ -214,8 +227,8 @@ __global__ void __launch_bounds__(BF_BLOCK) k_brute(RaysDev rays, const unsigned
             __syncthreads();
             const unsigned cnt = min((unsigned)BF_BLOCK, n_tris - t0);
             for (unsigned j = 0; j < cnt; ++j) {
-                float t, u, v;
-                if (mt_test(ox, oy, oz, dx, dy, dz, tmax, s_tri[j][0], s_tri[j][1], s_tri[j][2], t, u, v)) {
+                float t;
+                if (mt_hit(ox, oy, oz, dx, dy, dz, tmax, s_tri[j][0], s_tri[j][1], s_tri[j][2], t)) {
                     const unsigned long long k = hit_key(t, t0 + j);
                     bk = k < bk ? k : bk;
                 }

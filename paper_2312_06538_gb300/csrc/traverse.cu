@@ -475,17 +475,26 @@ __global__ void __launch_bounds__(256) k_emit(Parents par, StageBuf sb, PairOut 
                [&](unsigned p, unsigned s, unsigned, unsigned nch, unsigned nc, unsigned ob, unsigned ch, unsigned j,
                    bool valid) {
                    const unsigned t = valid ? par.tri(s, j) : 0u;
-                   for (unsigned c = 0; c < nc; ++c) {
-                       const unsigned w = ob + c * nch + ch;
-                       const unsigned m = sb.mask[w];
-                       if ((m >> lane) & 1u) store_pair(out, sb.pos[w] + __popc(m & lt), par.child_id(p, c), t);
+                   // lane c fetches child c's ballot and output position (all in flight at once)
+                   unsigned mc = 0, pc = 0;
+                   if ((unsigned)lane < nc) {
+                       const unsigned w = ob + lane * nch + ch;
+                       mc = sb.mask[w];
+                       pc = sb.pos[w];
+                   }
+                   unsigned any = __ballot_sync(FULL, mc != 0);
+                   while (any) {
+                       const int c = __ffs(any) - 1;
+                       any &= any - 1;
+                       const unsigned m = __shfl_sync(FULL, mc, c);
+                       const unsigned base = __shfl_sync(FULL, pc, c);
+                       if ((m >> lane) & 1u) store_pair(out, base + __popc(m & lt), par.child_id(p, c), t);
                    }
                    if (ch == 0 && (unsigned)lane < nc) {
                        // runs index the written list: clamp to its capacity (a list
                        // that overflowed is truncated and flagged CRSH_ERR_CAPACITY)
                        const unsigned c = lane, a = par.child_id(p, c);
-                       if (par.first_of_child(p, c))
-                           runs.start[a] = (unsigned)min((unsigned long long)sb.pos[ob + c * nch], out.cap);
+                       if (par.first_of_child(p, c)) runs.start[a] = (unsigned)min((unsigned long long)pc, out.cap);
                        if (par.last_of_child(p, c))
                            runs.end[a] = (unsigned)min((unsigned long long)sb.pos[ob + (c + 1) * nch], out.cap);
                    }
@@ -511,33 +520,35 @@ __global__ void k_runs_from_pairs(const uint32_t* node, const unsigned* p_count,
     }
 }
 
-// CSR offsets (n + 1) from the pair runs of a level: off[k] = pairs of nodes
-// before k (single block).
-__global__ void __launch_bounds__(1024) k_runs_to_csr(RunOut runs, const unsigned* n_count, uint32_t* off) {
-    __shared__ unsigned s_w[32];
-    __shared__ unsigned s_carry;
+// CSR offsets (n + 1) of the node-sorted level-1 list: a node's offset is the
+// start of its run; a node without pairs takes the start of the next node
+// with pairs (the list end if none).  A few steps forward over the runs find
+// it in the common case; longer gaps fall back to a binary search of the node
+// column.
+__global__ void k_runs_to_csr(RunOut runs, const uint32_t* node, const unsigned* n_count, const unsigned* p_count,
+                              unsigned long long cap, uint32_t* off) {
     const unsigned n = *n_count;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (unsigned base = 0; base < n; base += blockDim.x) {
-        const unsigned k = base + threadIdx.x;
-        const unsigned v = k < n ? runs.end[k] - runs.start[k] : 0u;
-        const unsigned inc = warp_incl_scan(v);
-        if (lane == 31) s_w[warp] = inc;
-        __syncthreads();
-        unsigned wpre = 0;
-        for (int i = 0; i < warp; ++i) wpre += s_w[i];
-        if (k < n) off[k] = s_carry + wpre + inc - v;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned t = 0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_w[i];
-            s_carry += t;
+    const unsigned total = (unsigned)min((unsigned long long)*p_count, cap);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) {
+        unsigned o = total;
+        bool found = false;
+        for (unsigned q = k; q < n && q < k + 8; ++q) {
+            if (runs.end[q] > runs.start[q]) {
+                o = runs.start[q];
+                found = true;
+                break;
+            }
         }
-        __syncthreads();
+        if (!found && k + 8 < n) {   // first pair whose node >= k
+            unsigned lo = 0, hi = total;
+            while (lo < hi) {
+                const unsigned mid = (lo + hi) >> 1;
+                if (node[mid] < k) lo = mid + 1; else hi = mid;
+            }
+            o = lo;
+        }
+        off[k] = o;
     }
-    if (threadIdx.x == 0) off[n] = s_carry;
 }
 
 // ---------------------------------------------------------------------------
@@ -676,7 +687,11 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
         run_stage(lp, w, tsph, pairs_of(l), w.runs[l - 1], ctr, (int)l - 1, B, dev, s);
         if (l == 1) break;
     }
-    k_runs_to_csr<<<1, 1024, 0, s>>>(w.runs[0], h->count, out->node_offsets);
+    {
+        const unsigned blocks = (h->capacity[0] + 256) / 256;
+        k_runs_to_csr<<<std::min<unsigned>(blocks, dev.sms * 8), 256, 0, s>>>(w.runs[0], out->node, h->count,
+                                                                              out->count, cap, out->node_offsets);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
 }
 
