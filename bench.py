@@ -52,7 +52,7 @@ def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -66,7 +66,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -201,13 +201,71 @@ def run_reference(args, w):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def closest_traffic():
+    """DRAM bytes per k_closest launch from the committed ncu summary, or None when
+    the kernel source changed since those counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_closest"]
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def launches_per_step(levels: int, compress: bool) -> int:
     """Kernels of libcrsh.so launched by one pass (count of <<<>>> in the call sequence)."""
     hash_sort = 3 + 1 + (1 if compress else 0) + 2 + 4 + (1 if compress else 0) + 1   # tables, gen, chunk, hist+plan, 4 passes, pos, gather
     build = levels
-    traverse = 1 + 4 + 5 * (levels - 1) + 1   # mesh stage, top stage, (csr + 4-kernel stage) per level, final csr
+    traverse = 1 + 5 + 1 + 5 * (levels - 1) + 1   # mesh stage, top stage + its runs, 5 kernels per level, csr
     closest = 3
     return hash_sort + build + traverse + closest
+
+
+def time_path(run, flush, stream, reps: int, warmup: int = 3) -> float:
+    """Mean ms of run() over reps, CUDA events on the stream, L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        flush.fill_(1)
+        run()
+    ts = []
+    for k in range(reps):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run()
+        b.record(stream)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ts) / reps
+
+
+def comparators(w, p, gstruct, lights, hp, bp, flush, stream, dev, n_rays):
+    """Same frame through the N x M brute force (after the same hash/sort) and through
+    the unsorted, no-mesh-culling mode (the RAH comparison of the paper)."""
+    import torch
+    from paper_2312_06538_gb300 import pipeline as pl
+    sh = stream.cuda_stream
+    out = {}
+
+    def brute():
+        p.hash_sort(gstruct, lights, hp, sh)
+        p.bruteforce(sh)
+    ms = time_path(brute, flush, stream, reps=3, warmup=1)
+    out["bruteforce"] = {"mrays_per_s": n_rays / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                         "tri_tests_per_ray": w.scene.n_tris}
+    q = pl.workload_pipeline(w, device=dev)
+    hp_rah, _ = pl.workload_params(w, sort=False)
+    c = q.run_fit(gstruct, lights, hp_rah, bp, mesh_cull=False)
+    ms = time_path(lambda: q.run(gstruct, lights, hp_rah, bp, mesh_cull=False, stream=sh), flush, stream, reps=5)
+    out["unsorted_no_mesh_cull"] = {"mrays_per_s": c["rays"] / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                                    "tri_tests_per_ray": c["final_tests"] / max(1, c["rays"]),
+                                    "all_tests_per_ray": (c["final_tests"] + sum(c["tests"])) / max(1, c["rays"])}
+    del q
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_gpu(args, w):
@@ -310,13 +368,7 @@ def run_gpu(args, w):
     achieved = c["final_tests"] * MT_FLOPS / (ch_ms * 1e-3) / 1e12
     tr_ms = float(stage[:, 2].mean())
     eq9_tests = sum(c["tests"]) + c["mesh_tests"]
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp):
-        try:
-            traffic = json.load(open(tp)).get("k_closest_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = closest_traffic()
     roofline = {"kernel": "crsh_closest_hit (k_closest + fill + finalize)", "bound": "alu",
                 "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
                 "traffic": traffic,
@@ -344,6 +396,11 @@ def run_gpu(args, w):
         "gpu_launches": launches_per_step(w.levels, True) * args.steps,
         "clocks": clocks,
     }
+    if not args.no_comparators:
+        try:
+            line["comparators"] = comparators(w, p, gstruct, lights, hp, bp, flush, stream, dev, n_rays)
+        except Exception as e:  # a comparator must not cost the main line
+            line["comparators"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
     if rank == 0:
@@ -355,7 +412,7 @@ def run_gpu(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", type=int, default=2)
@@ -363,6 +420,7 @@ def main():
     ap.add_argument("--ref-crop", type=int, default=128)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
     import synthetic

@@ -168,7 +168,7 @@ typedef struct {
     uint32_t *node, *tri;            /* capacity entries each */
     uint32_t *node_offsets;          /* level-1 node count + 1 entries: CSR over nodes */
     uint32_t *count;                 /* device: pairs written */
-    uint64_t capacity;
+    uint64_t capacity;               /* 1 .. 2^31 */
 } crsh_pairs;
 
 /* Closest hits in generation order (ray_id). tri = -1: no hit (t = u = v = 0). */

@@ -141,7 +141,7 @@ crsh_status crsh_traverse(const crsh_hierarchy* h, const crsh_scene* scene, cons
                           void* stream) {
     if (!hier_ok(h) || !scene_ok(scene, true) || !p || !out || !counters || !workspace) return CRSH_ERR_INVALID_ARG;
     if (!out->node || !out->tri || !out->node_offsets || !out->count || out->capacity == 0 ||
-        out->capacity > (1ull << 32) / h->bundle)
+        out->capacity > (1ull << 31))
         return CRSH_ERR_INVALID_ARG;
     DeviceInfo dev;
     if (!current_device(dev)) return CRSH_ERR_CUDA;

@@ -181,7 +181,7 @@ class Pipeline:
         self.traverse(mesh_cull, stream)
         self.closest_hit(stream)
 
-    def run_fit(self, gbuf, lights, hp, bp, mesh_cull=True, max_tries=4):
+    def run_fit(self, gbuf, lights, hp, bp, mesh_cull=True, max_tries=8):
         """run(), growing the pair lists until no level overflows (synchronises)."""
         for _ in range(max_tries):
             self.run(gbuf, lights, hp, bp, mesh_cull)

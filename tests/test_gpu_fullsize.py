@@ -1,0 +1,127 @@
+"""Full-size workloads in the launch configuration bench.py times.
+
+Config 2 (512x512, 60,162 triangles, ~0.5 M rays, B = 16, L = 4): every ray
+against the oracle (keys, order, hierarchy containment, per-level pair counts
+of the oracle's own full traversal, closest hits).  Config 3 (1024x1024,
+202,764 triangles, ~3 M rays): keys and order bit-exact, containment, the
+paper's counting identities, a seeded sample of rays against the oracle's
+brute force, and the hierarchy result bit-identical to the GPU brute force
+for every ray."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _gpu(w, pair_capacity=None):
+    from paper_2312_06538_gb300 import pipeline as pl
+    p = pl.workload_pipeline(w, pair_capacity=pair_capacity)
+    hp, bp = pl.workload_params(w)
+    g = p.gbuffer_struct(p.gbuffer_to_device(w.gbuffer))
+    lights = torch.from_numpy(w.lights).cuda() if w.lights.shape[0] else None
+    c = p.run_fit(g, lights, hp, bp)
+    return p, c
+
+
+def _front(w):
+    """Oracle ray generation, hash and sort (fast at any size)."""
+    rays = oracle.generate_rays(w.gbuffer, w.lights, w.shadow_cull)
+    keys = oracle.hash_keys(rays, w.hash_lo, w.hash_hi)
+    perm = oracle.stable_sort(keys)
+    return rays, keys, perm
+
+
+@pytest.fixture(scope="module")
+def c2():
+    w = synthetic.make(2)
+    p, c = _gpu(w)
+    ref = oracle.run_crsh(w.gbuffer, w.lights, w.shadow_cull, w.hash_lo, w.hash_hi, w.scene, w.bundle, w.levels,
+                          w.build_pads())
+    return w, p, c, ref
+
+
+def test_c2_keys_order_and_counts(c2):
+    w, p, c, ref = c2
+    got = p.sorted_rays()
+    assert c["rays"] == ref["counters"]["rays"] > 400_000
+    assert c["chunks"] == ref["counters"]["chunks"]
+    assert np.array_equal(got["ray_id"], ref["perm"])
+    assert np.array_equal(got["keys"], ref["keys"][ref["perm"]])
+    rc = ref["counters"]
+    for l in range(w.levels):
+        assert parity.within(c["hits"][l], rc["hits"][l], 1e-3), (l, c["hits"], rc["hits"])
+        assert parity.within(c["tests"][l], rc["tests"][l], 1e-3), (l, c["tests"], rc["tests"])
+    assert parity.within(c["final_tests"], rc["final_tests"], 1e-3)
+    assert c["mesh_tests"] == rc["mesh_tests"]
+
+
+def test_c2_hierarchy_contains_its_rays(c2):
+    w, p, c, ref = c2
+    lv = p.levels_host()
+    counts = [x[0].shape[0] for x in lv]
+    bad, worst = oracle.check_hierarchy(ref["sorted_rays"], w.bundle, counts, np.concatenate([x[0] for x in lv]),
+                                        np.concatenate([x[1] for x in lv]))
+    assert bad == 0, (bad, worst)
+
+
+def test_c2_closest_hits_every_ray(c2):
+    w, p, c, ref = c2
+    rep = parity.compare_hits(p.hits_host(), ref["hits"], ref["rays"], w.scene.verts)
+    parity.check_report(rep)
+    idx = np.random.default_rng(2).choice(c["rays"], size=1500, replace=False)
+    sub = {k: np.ascontiguousarray(v[idx]) for k, v in ref["rays"].items()}
+    assert np.array_equal(oracle.bruteforce(sub, w.scene.verts)[0], ref["hits"][0][idx])
+
+
+def test_c2_equals_gpu_bruteforce(c2):
+    w, p, c, ref = c2
+    a = [x.copy() for x in p.hits_host()]
+    p.bruteforce()
+    for x, y in zip(a, p.hits_host()):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+
+
+@pytest.fixture(scope="module")
+def c3():
+    w = synthetic.make(3)
+    p, c = _gpu(w, pair_capacity=1 << 27)
+    return w, p, c
+
+
+def test_c3_keys_order_identities_and_containment(c3):
+    w, p, c = c3
+    rays, keys, perm = _front(w)
+    got = p.sorted_rays()
+    assert c["rays"] == rays["ox"].shape[0] > 2_000_000
+    assert np.array_equal(got["ray_id"], perm)
+    assert np.array_equal(got["keys"], keys[perm])
+    assert c["chunks"] == oracle.chunk_count(keys)
+    for l in range(w.levels - 1):
+        assert c["tests_paper"][l] == w.bundle * c["hits"][l + 1]
+    assert c["final_tests_paper"] == w.bundle * c["hits"][0]
+    srays = oracle.gather(rays, perm)
+    lv = p.levels_host()
+    bad, worst = oracle.check_hierarchy(srays, w.bundle, [x[0].shape[0] for x in lv],
+                                        np.concatenate([x[0] for x in lv]), np.concatenate([x[1] for x in lv]))
+    assert bad == 0, (bad, worst)
+
+
+def test_c3_sampled_hits_and_gpu_bruteforce(c3):
+    w, p, c = c3
+    rays, _, _ = _front(w)
+    hits = [x.copy() for x in p.hits_host()]
+    idx = np.sort(np.random.default_rng(3).choice(c["rays"], size=800, replace=False))
+    sub = {k: np.ascontiguousarray(v[idx]) for k, v in rays.items()}
+    bf = oracle.bruteforce(sub, w.scene.verts)
+    rep = parity.compare_hits(tuple(h[idx] for h in hits), bf, sub, w.scene.verts)
+    parity.check_report(rep)
+    assert rep["hits"] > 100
+    p.bruteforce()
+    for x, y in zip(hits, p.hits_host()):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
