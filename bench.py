@@ -268,6 +268,30 @@ def comparators(w, p, gstruct, lights, hp, bp, flush, stream, dev, n_rays):
     return out
 
 
+def adjoint_timing(dev, flush, stream, reps: int = 10):
+    """Backward (crsh_closest_hit_backward) vs forward closest hit on the adjoint workload:
+    2^20 reflection rays of a 1024x1024 all-mirror frame, 99,842 triangles (config 5)."""
+    import synthetic
+    import torch
+    from paper_2312_06538_gb300 import pipeline as pl
+    w5 = synthetic.make(5)
+    p5 = pl.workload_pipeline(w5, device=dev)
+    hp5, bp5 = pl.workload_params(w5)
+    g5 = p5.gbuffer_struct(p5.gbuffer_to_device(w5.gbuffer, dev))
+    c5 = p5.run_fit(g5, None, hp5, bp5)
+    n = c5["rays"]
+    z = torch.randn((3, p5.ray_capacity), generator=torch.Generator().manual_seed(1005)).to(dev)
+    sh = stream.cuda_stream
+    fwd = time_path(lambda: p5.closest_hit(sh), flush, stream, reps)
+    bwd = time_path(lambda: p5.backward(z[0], z[1], z[2], sh), flush, stream, reps)
+    out = {"workload": f"{n} reflection rays, {w5.scene.n_tris:,} triangles (1024x1024 all-mirror frame)",
+           "backward_ms": bwd, "forward_closest_hit_ms": fwd, "backward_over_forward": bwd / fwd,
+           "hit_rays": int((p5.hit_tri[:n] >= 0).sum().item())}
+    del p5
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -401,6 +425,11 @@ def run_gpu(args, w):
             line["comparators"] = comparators(w, p, gstruct, lights, hp, bp, flush, stream, dev, n_rays)
         except Exception as e:  # a comparator must not cost the main line
             line["comparators"] = {"error": f"{type(e).__name__}: {e}"}
+    if not args.no_adjoint:
+        try:
+            line["adjoint"] = adjoint_timing(dev, flush, stream)
+        except Exception as e:
+            line["adjoint"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
     if rank == 0:
@@ -421,6 +450,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
     import synthetic

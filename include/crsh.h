@@ -251,6 +251,30 @@ crsh_status crsh_closest_hit(const crsh_hierarchy *h, const crsh_rays *rays, con
                              crsh_counters *counters, void *workspace, size_t workspace_bytes,
                              void *stream);
 
+/* Workspace bytes crsh_closest_hit_backward needs. */
+size_t crsh_closest_hit_backward_workspace(uint32_t ray_capacity);
+
+/* Gradients of the closest hits with respect to the triangle vertices and the
+ * ray origins and directions (the paper has no backward pass: this is the
+ * adjoint of the final test of Section 3.3.8, with which-triangle-is-hit held
+ * fixed).  For a ray o + t d hitting triangle (V0, V1, V2) at (u, v) and an
+ * upstream gradient g = dL/d(t, u, v) (g_t, g_u, g_v: device, generation
+ * order, one float per ray), with A = [-d | e1 | e2] and lambda = A^-T g:
+ *   g_orig = lambda, g_dir = t lambda,
+ *   g_verts: V0 += -(1-u-v) lambda, V1 += -u lambda, V2 += -v lambda,
+ * summed over the rays that hit each triangle.
+ * rays / n_rays / hits: as produced by crsh_hash_sort and crsh_closest_hit.
+ * Outputs (device, overwritten; zero where no hit): g_verts 9 floats per
+ * triangle (V0 xyz, V1 xyz, V2 xyz); g_orig and g_dir 3 floats per ray in
+ * generation order, sized for rays->capacity.  FP32.  The per-triangle sums
+ * are a stable sort by triangle plus a segmented reduction in a fixed order:
+ * no atomics, identical bits on every run.  counters may be NULL (it only
+ * receives a device status). */
+crsh_status crsh_closest_hit_backward(const crsh_rays *rays, const uint32_t *n_rays, const crsh_scene *scene,
+                                      const crsh_hits *hits, const float *g_t, const float *g_u, const float *g_v,
+                                      float *g_verts, float *g_orig, float *g_dir, crsh_counters *counters,
+                                      void *workspace, size_t workspace_bytes, void *stream);
+
 /* crsh_closest_hit without a caller-supplied workspace.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory - code that runs while a CUDA graph is being captured (where

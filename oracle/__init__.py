@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_bruteforce.argtypes = [I64] + [P] * 7 + [I64, P, P, P, P, P]
         L.oracle_final.restype = None
         L.oracle_final.argtypes = [I64, P, P, U32, I64] + [P] * 9 + [P, P, P, P, ctypes.POINTER(_Counters)]
+        L.oracle_adjoint.restype = None
+        L.oracle_adjoint.argtypes = [I64] + [P] * 6 + [P, P, P, P, P, P, P, I64, P, P, P, P]
         L.oracle_check_hierarchy.restype = I64
         L.oracle_check_hierarchy.argtypes = [I64] + [P] * 6 + [U32, U32, P, P, P, P]
         _lib = L
@@ -295,3 +297,20 @@ def run_crsh(gbuffer, lights, shadow_cull, lo, hi, scene, B, L, pads, mesh_cull=
     ctr["chunks"] = chunk_count(keys)
     return dict(rays=rays, keys=keys, perm=perm, sorted_rays=srays, levels=levels, pair_node=pn,
                 pair_tri=pt, hits=hits, counters=ctr)
+
+
+def adjoint(rays: Dict[str, np.ndarray], hits, g_t, g_u, g_v, verts: np.ndarray):
+    """FP64 gradients of the closest hit with the hit assignment fixed (implicit-function
+    closed form): returns (g_verts (T, 9), g_orig (N, 3), g_dir (N, 3))."""
+    r = {k: _c(rays[k], np.float32) for k in ("ox", "oy", "oz", "dx", "dy", "dz")}
+    tri = _c(hits[0], np.int32)
+    t, u, w = (_c(x, np.float64) for x in hits[1:4])
+    gt, gu, gv = (_c(x, np.float64) for x in (g_t, g_u, g_v))
+    v = _c(verts, np.float32)
+    n = tri.shape[0]
+    g_verts = np.empty((v.shape[0], 9), np.float64)
+    g_orig = np.empty((n, 3), np.float64)
+    g_dir = np.empty((n, 3), np.float64)
+    lib().oracle_adjoint(n, *[_p(r[k]) for k in ("ox", "oy", "oz", "dx", "dy", "dz")], _p(tri), _p(t), _p(u), _p(w),
+                         _p(gt), _p(gu), _p(gv), v.shape[0], _p(v), _p(g_verts), _p(g_orig), _p(g_dir))
+    return g_verts, g_orig, g_dir

@@ -709,3 +709,54 @@ int64_t oracle_check_hierarchy(int64_t n, const float* ox, const float* oy, cons
     if (worst) *worst = w;
     return bad;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of the closest hit (not a step of the paper: the adjoint of the  */
+/* final test, Section 3.3.8, with the hit assignment held fixed).            */
+/* ------------------------------------------------------------------------ */
+/* For a ray o + t d hitting triangle (V0, V1, V2) at barycentrics (u, v),
+ * F = o + t d - V0 - u (V1 - V0) - v (V2 - V0) = 0 defines (t, u, v)
+ * implicitly.  With A = [-d | e1 | e2] (columns) and an upstream gradient
+ * g = dL/d(t, u, v), the implicit-function theorem gives lambda = A^-T g and
+ *   dL/do = lambda, dL/dd = t lambda,
+ *   dL/dV0 = -(1 - u - v) lambda, dL/dV1 = -u lambda, dL/dV2 = -v lambda.
+ * A^T lambda = g is solved here by Cramer's rule with 3x3 determinants.
+ * Rays with tri < 0 contribute nothing.  FP64 throughout. */
+static double det3(const double m[3][3]) {
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+void oracle_adjoint(int64_t n, const float* ox, const float* oy, const float* oz, const float* dx, const float* dy,
+                    const float* dz, const int32_t* tri, const double* t, const double* u, const double* v,
+                    const double* g_t, const double* g_u, const double* g_v, int64_t n_tris, const float* verts,
+                    double* g_verts, double* g_orig, double* g_dir) {
+    (void)ox; (void)oy; (void)oz;
+    for (int64_t k = 0; k < 9 * n_tris; ++k) g_verts[k] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int c = 0; c < 3; ++c) g_orig[3 * i + c] = g_dir[3 * i + c] = 0.0;
+        if (tri[i] < 0) continue;
+        const float* V = verts + 9 * (int64_t)tri[i];
+        double e1[3], e2[3], d[3] = {dx[i], dy[i], dz[i]};
+        for (int c = 0; c < 3; ++c) { e1[c] = (double)V[3 + c] - V[c]; e2[c] = (double)V[6 + c] - V[c]; }
+        /* A^T: rows -d, e1, e2 */
+        double M[3][3], g[3] = {g_t[i], g_u[i], g_v[i]}, lam[3];
+        for (int c = 0; c < 3; ++c) { M[0][c] = -d[c]; M[1][c] = e1[c]; M[2][c] = e2[c]; }
+        double D = det3(M);
+        if (D == 0.0) continue;
+        for (int col = 0; col < 3; ++col) {
+            double Mc[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) Mc[r][c] = (c == col) ? g[r] : M[r][c];
+            lam[col] = det3(Mc) / D;
+        }
+        double w0 = -(1.0 - u[i] - v[i]), w1 = -u[i], w2 = -v[i];
+        for (int c = 0; c < 3; ++c) {
+            g_orig[3 * i + c] = lam[c];
+            g_dir[3 * i + c] = t[i] * lam[c];
+            g_verts[9 * (int64_t)tri[i] + c] += w0 * lam[c];
+            g_verts[9 * (int64_t)tri[i] + 3 + c] += w1 * lam[c];
+            g_verts[9 * (int64_t)tri[i] + 6 + c] += w2 * lam[c];
+        }
+    }
+}

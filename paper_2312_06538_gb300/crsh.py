@@ -94,6 +94,10 @@ SIGNATURES = [
     ("crsh_closest_hit", ctypes.c_int,
      [ctypes.POINTER(crsh_hierarchy), ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_scene),
       ctypes.POINTER(crsh_pairs), ctypes.POINTER(crsh_hits), P, P, ctypes.c_size_t, P]),
+    ("crsh_closest_hit_backward_workspace", ctypes.c_size_t, [U32]),
+    ("crsh_closest_hit_backward", ctypes.c_int,
+     [ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_scene), ctypes.POINTER(crsh_hits), P, P, P, P, P, P, P, P,
+      ctypes.c_size_t, P]),
     ("crsh_closest_hit_noalloc", ctypes.c_int,
      [ctypes.POINTER(crsh_hierarchy), ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_scene),
       ctypes.POINTER(crsh_pairs), ctypes.POINTER(crsh_hits), P, P]),
@@ -200,3 +204,16 @@ def crsh_closest_hit_noalloc(h: crsh_hierarchy, rays: crsh_rays, n_rays: int, sc
     _check("crsh_closest_hit_noalloc",
            load().crsh_closest_hit_noalloc(ctypes.byref(h), ctypes.byref(rays), P(n_rays), ctypes.byref(scene),
                                            ctypes.byref(pairs), ctypes.byref(out), P(counters), P(stream)))
+
+
+def crsh_closest_hit_backward_workspace(ray_capacity: int) -> int:
+    return load().crsh_closest_hit_backward_workspace(ray_capacity)
+
+
+def crsh_closest_hit_backward(rays: crsh_rays, n_rays: int, scene: crsh_scene, hits: crsh_hits, g_t: int, g_u: int,
+                              g_v: int, g_verts: int, g_orig: int, g_dir: int, counters: int, workspace: int,
+                              workspace_bytes: int, stream: int):
+    _check("crsh_closest_hit_backward",
+           load().crsh_closest_hit_backward(ctypes.byref(rays), P(n_rays), ctypes.byref(scene), ctypes.byref(hits),
+                                            P(g_t), P(g_u), P(g_v), P(g_verts), P(g_orig), P(g_dir), P(counters),
+                                            P(workspace), workspace_bytes, P(stream)))

@@ -176,6 +176,21 @@ crsh_status crsh_closest_hit_noalloc(const crsh_hierarchy* h, const crsh_rays* r
                                       static_cast<cudaStream_t>(stream), dev);
 }
 
+size_t crsh_closest_hit_backward_workspace(uint32_t ray_capacity) { return backward_workspace(ray_capacity); }
+
+crsh_status crsh_closest_hit_backward(const crsh_rays* rays, const uint32_t* n_rays, const crsh_scene* scene,
+                                      const crsh_hits* hits, const float* g_t, const float* g_u, const float* g_v,
+                                      float* g_verts, float* g_orig, float* g_dir, crsh_counters* counters,
+                                      void* workspace, size_t workspace_bytes, void* stream) {
+    if (!rays_ok(rays) || !n_rays || !scene_ok(scene, false) || !hits || !hits->tri || !hits->t || !hits->u ||
+        !hits->v || !g_t || !g_u || !g_v || !g_verts || !g_orig || !g_dir || !workspace)
+        return CRSH_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if (!current_device(dev)) return CRSH_ERR_CUDA;
+    return backward_launch(rays, n_rays, scene, hits, g_t, g_u, g_v, g_verts, g_orig, g_dir, counters, workspace,
+                           workspace_bytes, static_cast<cudaStream_t>(stream), dev);
+}
+
 crsh_status crsh_bruteforce_closest_hit(const crsh_rays* rays, const uint32_t* n_rays, const crsh_scene* scene,
                                         crsh_hits* out, void* workspace, size_t workspace_bytes, void* stream) {
     if (!rays_ok(rays) || !n_rays || !scene_ok(scene, true) || !out || !out->tri || !out->t || !out->u || !out->v ||

@@ -487,6 +487,26 @@ __global__ void __launch_bounds__(RS_BLOCK) k_radix_pass(int pass, uint32_t* kA,
 }
 static_assert(RS_BLOCK == 256, "one thread per digit");
 
+size_t radix_status_words(uint32_t cap) {
+    const size_t rs_tiles = ((size_t)cap + RS_TILE - 1) / RS_TILE + 1;
+    return 4 * rs_tiles * 256;
+}
+
+// Stable LSD sort of (kA, vA)[0 .. *cnt) by key, kB/vB as the other buffer.
+// rw.hist, rw.tile_ctr (4) and rw.status must be zero; rw.plan[4] tells which
+// buffer holds the result (0: A, 1: B).
+void radix_sort_launch(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, const unsigned* cnt_ptr, uint32_t cap,
+                       const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev) {
+    const unsigned cap_tiles = (cap + RS_TILE - 1) / RS_TILE;
+    k_radix_hist<<<dev.sms * 2, 256, 0, s>>>(kA, cnt_ptr, rw.hist);
+    k_radix_plan<<<1, 256, 0, s>>>(rw.hist, cnt_ptr, rw.offs, rw.plan, 1);
+    const unsigned grid = cap_tiles < (unsigned)(dev.sms * 4) ? (cap_tiles ? cap_tiles : 1) : dev.sms * 4;
+    const size_t rs_tiles = (size_t)cap_tiles + 1;
+    for (int p = 0; p < 4; ++p)
+        k_radix_pass<<<grid, RS_BLOCK, 0, s>>>(p, kA, vA, kB, vB, cnt_ptr, rw.offs, rw.plan,
+                                                rw.status + (size_t)p * rs_tiles * 256, &rw.tile_ctr[p], ctr);
+}
+
 // ---------------------------------------------------------------------------
 // Section 3.3.5: decompression.  Chunk sizes in sorted order, exclusive scan
 // (the skeleton), then every sorted position finds its chunk.
@@ -650,12 +670,11 @@ HashWs carve_hash(void* ws, uint32_t cap, uint32_t max_pixels) {
     w.plan = c.take<unsigned>(8);
     const size_t gen_tiles = ((size_t)max_pixels + GEN_BLOCK - 1) / GEN_BLOCK + 1;
     const size_t cmp_tiles = ((size_t)cap + CMP_TILE - 1) / CMP_TILE + 1;
-    const size_t rs_tiles = ((size_t)cap + RS_TILE - 1) / RS_TILE + 1;
     const size_t sc_tiles = ((size_t)cap + SCAN_TILE - 1) / SCAN_TILE + 1;
     w.st_gen = c.take<unsigned long long>(gen_tiles);
     w.st_chunk = c.take<unsigned long long>(cmp_tiles);
     w.st_pos = c.take<unsigned long long>(sc_tiles);
-    w.st_radix = c.take<unsigned>(4 * rs_tiles * 256);
+    w.st_radix = c.take<unsigned>(radix_status_words(cap));
     w.ctl_begin = ws ? reinterpret_cast<char*>(ws) + ctl0 : nullptr;
     w.ctl_bytes = c.off - ctl0;
     w.total = c.off + 256;
@@ -727,7 +746,6 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
 
     const bool sort = hp->sort != 0;
     const bool compress = sort && hp->compress != 0;
-    const unsigned cap_tiles_rs = (cap + RS_TILE - 1) / RS_TILE;
     uint32_t *kA = w.gen.key, *vA = w.gen.val;
     const unsigned* cnt_ptr = n_out;
     if (compress) {
@@ -740,13 +758,8 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
         cnt_ptr = &w.counts[0];
     }
     if (sort) {
-        k_radix_hist<<<dev.sms * 2, 256, 0, s>>>(kA, cnt_ptr, w.hist);
-        k_radix_plan<<<1, 256, 0, s>>>(w.hist, cnt_ptr, w.offs, w.plan, 1);
-        unsigned grid = cap_tiles_rs < (unsigned)(dev.sms * 4) ? (cap_tiles_rs ? cap_tiles_rs : 1) : dev.sms * 4;
-        const size_t rs_tiles = (size_t)cap_tiles_rs + 1;
-        for (int p = 0; p < 4; ++p)
-            k_radix_pass<<<grid, RS_BLOCK, 0, s>>>(p, kA, vA, w.altK, w.altV, cnt_ptr, w.offs, w.plan,
-                                                    w.st_radix + (size_t)p * rs_tiles * 256, &w.tile_ctr[2 + p], ctr);
+        RadixWs rw{w.hist, w.offs, w.plan, &w.tile_ctr[2], w.st_radix};
+        radix_sort_launch(kA, vA, w.altK, w.altV, cnt_ptr, cap, rw, ctr, s, dev);
     } else {
         k_radix_plan<<<1, 256, 0, s>>>(w.hist, cnt_ptr, w.offs, w.plan, 0);
     }

@@ -22,6 +22,18 @@ struct TableChunk {
     float v[kMax];
 };
 
+// One-sweep LSD radix sort of 32-bit (key, value) pairs (hash_sort.cu).
+struct RadixWs {
+    unsigned* hist;      // 4 x 256, zeroed
+    unsigned* offs;      // 4 x 256
+    unsigned* plan;      // 5; plan[4] = buffer holding the result (0: A, 1: B)
+    unsigned* tile_ctr;  // 4, zeroed
+    unsigned* status;    // radix_status_words(cap), zeroed
+};
+size_t radix_status_words(uint32_t cap);
+void radix_sort_launch(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, const unsigned* cnt_ptr, uint32_t cap,
+                       const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev);
+
 size_t hash_sort_workspace(uint32_t capacity, uint32_t max_pixels);
 crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, const float* lights, uint32_t n_lights,
                              const crsh_hash_params* hp, crsh_rays* out, uint32_t* keys_out, uint32_t* n_out,
@@ -44,6 +56,11 @@ crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, c
 crsh_status closest_hit_noalloc_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
                                        const crsh_scene* sc, const crsh_pairs* pairs, crsh_hits* out,
                                        crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev);
+size_t backward_workspace(uint32_t ray_capacity);
+crsh_status backward_launch(const crsh_rays* rays, const uint32_t* n_rays, const crsh_scene* sc, const crsh_hits* hits,
+                            const float* g_t, const float* g_u, const float* g_v, float* g_verts, float* g_orig,
+                            float* g_dir, crsh_counters* ctr, void* ws, size_t ws_bytes, cudaStream_t s,
+                            const DeviceInfo& dev);
 crsh_status bruteforce_launch(const crsh_rays* rays, const uint32_t* n_rays, const crsh_scene* sc, crsh_hits* out,
                               void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev);
 

@@ -172,6 +172,23 @@ class Pipeline:
         C.crsh_bruteforce_closest_hit(self.rays, _ptr(self.n_rays), self.scene, self.hits, _ptr(self.ws_hit),
                                       self.ws_hit_bytes, stream)
 
+    def backward(self, g_t: torch.Tensor, g_u: torch.Tensor, g_v: torch.Tensor, stream: Optional[int] = None):
+        """Gradients of the current hits (crsh_closest_hit_backward): upstream gradients in
+        generation order -> (g_verts (T, 9), g_orig (capacity, 3), g_dir (capacity, 3))."""
+        stream = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
+        dev = self.device
+        if getattr(self, "ws_bw", None) is None:
+            self.ws_bw_bytes = C.crsh_closest_hit_backward_workspace(self.ray_capacity)
+            self.ws_bw = torch.empty(self.ws_bw_bytes, dtype=torch.uint8, device=dev)
+        g_verts = torch.empty((self.n_tris, 9), dtype=torch.float32, device=dev)
+        g_orig = torch.empty((self.ray_capacity, 3), dtype=torch.float32, device=dev)
+        g_dir = torch.empty((self.ray_capacity, 3), dtype=torch.float32, device=dev)
+        gt, gu, gv = (x.contiguous().float() for x in (g_t, g_u, g_v))
+        C.crsh_closest_hit_backward(self.rays, _ptr(self.n_rays), self.scene, self.hits, _ptr(gt), _ptr(gu), _ptr(gv),
+                                    _ptr(g_verts), _ptr(g_orig), _ptr(g_dir), _ptr(self.counters), _ptr(self.ws_bw),
+                                    self.ws_bw_bytes, stream)
+        return g_verts, g_orig, g_dir
+
     def run(self, gbuf: C.crsh_gbuffer, lights: Optional[torch.Tensor], hp: C.crsh_hash_params,
             bp: C.crsh_build_params, mesh_cull: bool = True, stream: Optional[int] = None):
         """One pass of the whole path (asynchronous)."""

@@ -528,3 +528,81 @@ def test_traversal_pairs_equal_ancestor_brute_force():
     assert got == want and len(want) > 0
     order = list(zip(res["pair_node"].tolist(), res["pair_tri"].tolist()))
     assert order == sorted(order)
+
+
+# --------------------------------------------------------------------------
+# Adjoint of the closest hit (hit assignment fixed): central finite differences
+# --------------------------------------------------------------------------
+
+def _loss_fd(o, d, tri_v, w):
+    h, t, u, v = oracle.mt(o, d, np.inf, tri_v)
+    assert h
+    return w[0] * t + w[1] * u + w[2] * v
+
+
+def test_adjoint_matches_central_differences():
+    """dL/d(o, d, V) of L = w_t t + w_u u + w_v v against FP64 central differences of the oracle's own
+    Moller-Trumbore (h = 1e-5 on float64 inputs, where truncation is far below the tolerance)."""
+    rng = np.random.default_rng(11)
+    checked = 0
+    for _ in range(60):
+        tri_v = rng.uniform(-1, 1, (3, 3))
+        bary = rng.dirichlet([2, 2, 2])
+        target = bary @ tri_v
+        o = rng.uniform(-3, 3, 3)
+        d = target - o
+        d = d / np.linalg.norm(d)
+        h, t, u, v = oracle.mt(o, d, np.inf, tri_v.astype(np.float32))
+        if not h or min(u, v, 1 - u - v) < 5e-2:
+            continue
+        w = rng.normal(size=3)
+        rays = {"ox": np.array([o[0]], np.float32), "oy": np.array([o[1]], np.float32),
+                "oz": np.array([o[2]], np.float32), "dx": np.array([d[0]], np.float32),
+                "dy": np.array([d[1]], np.float32), "dz": np.array([d[2]], np.float32)}
+        o32 = np.array([rays[k][0] for k in ("ox", "oy", "oz")], np.float64)
+        d32 = np.array([rays[k][0] for k in ("dx", "dy", "dz")], np.float64)
+        v32 = tri_v.astype(np.float32)
+        h, t, u, v = oracle.mt(o32, d32, np.inf, v32)
+        gv_, go, gd = oracle.adjoint(rays, (np.array([0], np.int32), np.array([t]), np.array([u]), np.array([v])),
+                                     [w[0]], [w[1]], [w[2]], v32[None])
+
+        def fd(f, x, eps=1e-5):
+            g = np.zeros_like(x)
+            for k in range(x.size):
+                a, b = x.copy(), x.copy()
+                a.flat[k] += eps
+                b.flat[k] -= eps
+                g.flat[k] = (f(a) - f(b)) / (2 * eps)
+            return g
+
+        # float64 finite differences through a float64 copy of the test (oracle.mt reads float64 rays,
+        # float32 vertices: perturb vertices through exact float64 -> the vertex FD uses numpy's solve)
+        def mt64(oo, dd, vv):
+            A = np.stack([-dd, vv[1] - vv[0], vv[2] - vv[0]], 1)
+            tt, uu, ww = np.linalg.solve(A, oo - vv[0])
+            return w[0] * tt + w[1] * uu + w[2] * ww
+        V = v32.astype(np.float64)
+        ref_o = fd(lambda x: mt64(x, d32, V), o32)
+        ref_d = fd(lambda x: mt64(o32, x, V), d32)
+        ref_v = fd(lambda x: mt64(o32, d32, x.reshape(3, 3)), V.reshape(-1))
+        scale = max(1.0, np.abs(ref_v).max(), np.abs(ref_o).max(), np.abs(ref_d).max())
+        assert np.abs(go[0] - ref_o).max() <= 1e-4 * scale
+        assert np.abs(gd[0] - ref_d).max() <= 1e-4 * scale
+        assert np.abs(gv_[0] - ref_v).max() <= 1e-4 * scale
+        checked += 1
+    assert checked > 20
+
+
+def test_adjoint_accumulates_per_triangle_and_skips_misses():
+    tri_v = np.array([[0, 0, 5], [1, 0, 5], [0, 1, 5]], np.float32)
+    rays = {"ox": np.array([0.2, 0.1, 5.0], np.float32), "oy": np.array([0.3, 0.1, 5.0], np.float32),
+            "oz": np.zeros(3, np.float32), "dx": np.zeros(3, np.float32), "dy": np.zeros(3, np.float32),
+            "dz": np.ones(3, np.float32)}
+    hits = (np.array([0, 0, -1], np.int32), np.array([5.0, 5.0, 0]), np.array([0.2, 0.1, 0]), np.array([0.3, 0.1, 0]))
+    gv_, go, gd = oracle.adjoint(rays, hits, np.ones(3), np.zeros(3), np.zeros(3), tri_v[None])
+    # dt/do_z = -1 for a plane z = 5 hit from below along +z; dt/do_x = dt/do_y = 0
+    assert go[0] == pytest.approx([0, 0, -1]) and go[1] == pytest.approx([0, 0, -1])
+    assert (go[2] == 0).all() and (gd[2] == 0).all()
+    assert gd[0] == pytest.approx([0, 0, -5])
+    # translating the triangle by +z moves t by +1: the three corner gradients sum to (0, 0, 1) per ray
+    assert gv_[0].reshape(3, 3).sum(0) == pytest.approx([0, 0, 2])
