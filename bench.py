@@ -292,6 +292,67 @@ def adjoint_timing(dev, flush, stream, reps: int = 10):
     return out
 
 
+def batched_comparison(dev, n_batches=32, reps=5):
+    """32 ray batches of log-uniform size (2^11 .. 2^20 rays) over 8 scenes of 5k..200k
+    triangles: the batched pipeline (autotuned B, L per size class, one CUDA graph over 8
+    streams) against the plain pipeline run per batch (B = 16, L = 4, one stream)."""
+    import math
+    import synthetic
+    import torch
+    from paper_2312_06538_gb300 import batched as bt
+    from paper_2312_06538_gb300 import pipeline as pl
+    spec = synthetic.config4_batches(n_batches)
+    batches, frames = [], {}
+    t0 = time.perf_counter()
+    for n, k in spec:
+        res = max(16, int(math.ceil(math.sqrt(n))))
+        while True:
+            wk = synthetic.config4_frame(k, res)
+            rays, got = bt.secondary_rays(wk.scene, wk.gbuffer, wk.lights, n, wk.hash_lo, wk.hash_hi, device=dev)
+            if got >= n:
+                break
+            res = int(res * 1.3) + 1
+        frames[id(wk.scene)] = wk
+        batches.append((wk.scene, rays, n))
+    prep_s = time.perf_counter() - t0
+    pads_of = lambda sc: frames[id(sc)].build_pads()  # noqa: E731
+    hp_of = lambda sc: pl.hash_params(frames[id(sc)].hash_lo, frames[id(sc)].hash_hi)  # noqa: E731
+    t0 = time.perf_counter()
+    tuner = bt.Autotuner()
+    bat = bt.BatchedCRSH(batches, pads_of, hp_of, tuner=tuner, n_streams=8, device=dev)
+    tune_s = time.perf_counter() - t0
+    plain = bt.PlainBatches(batches, pads_of, hp_of, device=dev)
+    bat.capture()
+    total = sum(n for _, _, n in batches)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t)
+        return sorted(ts)[len(ts) // 2]
+    tp = timed(plain.run)
+    tb = timed(bat.replay)
+    identical = all(torch.equal(x.view(torch.int32), y.view(torch.int32))
+                    for a, b in zip(bat.runs, plain.runs) for x, y in zip(a.hits(), b.hits()))
+    out = {"workload": f"{len(batches)} batches, {total:,} rays, sizes {min(n for n, _ in spec)}..{max(n for n, _ in spec)}, "
+                       f"8 scenes of 5k..200k triangles",
+           "plain_mrays_per_s": total / tp / 1e6, "batched_mrays_per_s": total / tb / 1e6,
+           "batched_over_plain": tp / tb, "identical_hits": bool(identical),
+           "plain_ms": 1e3 * tp, "batched_ms": 1e3 * tb, "timing": "host wall clock around the whole set, synchronised",
+           "tuned": {str(k): list(v) for k, v in sorted(tuner.table.items())},
+           "prep_s": prep_s, "tune_s": tune_s}
+    del bat, plain
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -425,6 +486,11 @@ def run_gpu(args, w):
             line["comparators"] = comparators(w, p, gstruct, lights, hp, bp, flush, stream, dev, n_rays)
         except Exception as e:  # a comparator must not cost the main line
             line["comparators"] = {"error": f"{type(e).__name__}: {e}"}
+    if not args.no_batched:
+        try:
+            line["batched"] = batched_comparison(dev)
+        except Exception as e:
+            line["batched"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_adjoint:
         try:
             line["adjoint"] = adjoint_timing(dev, flush, stream)
@@ -451,6 +517,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
     import synthetic

@@ -251,6 +251,50 @@ def config5(res: Optional[int] = None) -> Workload:
                    lights, 16, 4, True, config5.__doc__)
 
 
+def config4_scene(k: int) -> Scene:
+    """Scene k of the batched workload: a room box plus icospheres / tori / displaced spheres,
+    about 5,000 * 40^(k/7) triangles (5k .. 200k, log-spaced), 30 % mirror, 20 % glass."""
+    target = 5000.0 * 40.0 ** (k / 7.0)
+    n_big = int(target * 0.6 // 5120)                      # icospheres(4)
+    rest = target - 5120 * n_big
+    n_tor = int(rest * 0.5 // 768)                         # tori 24x16
+    n_disp = max(1, int((rest - 768 * n_tor) // 1280))     # displaced icospheres(3)
+    eye = np.array([0.0, 1.0, 3.5])
+    _, scene = _objects_scene(1040 + k, n_big, 4, n_tor, (24, 16), n_disp, -3, 3, 0.3, 0.2, "room", avoid=eye)
+    return scene
+
+
+def config4_frame(k: int, res: int):
+    """Primary-hit buffer of scene k at res x res, 2 lights (the camera and lights of config 3)."""
+    scene = config4_scene_cached(k)
+    root = SplitMix64(1040 + k)
+    lights = _lights(root, 2, scene.mesh_sphere[1:], 3.5, 1.0, 3.5)
+    cam = _camera(np.array([0.0, 1.0, 3.5]), (0, 0, 0), 60.0, res, res)
+    return _finish(f"batched scene {k} at {res}x{res}", res, res, scene, cam, lights, 16, 4, True,
+                   config4_frame.__doc__)
+
+
+_c4_cache: Dict[int, Scene] = {}
+
+
+def config4_scene_cached(k: int) -> Scene:
+    if k not in _c4_cache:
+        _c4_cache[k] = config4_scene(k)
+    return _c4_cache[k]
+
+
+def config4_batches(n_batches: int = 32, lo: int = 1 << 11, hi: int = 1 << 20):
+    """The batched workload: (ray count, scene index) per batch; sizes floor(exp(U[ln lo, ln hi])),
+    scene drawn uniformly from the 8 scenes (seed 1004)."""
+    rng = SplitMix64(1004)
+    out = []
+    for _ in range(n_batches):
+        size = int(np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        k = int(rng.uniform() * 8) % 8
+        out.append((size, k))
+    return out
+
+
 CONFIGS = {1: config1, 2: config2, 3: config3, 5: config5}
 
 
