@@ -2,12 +2,11 @@
 // data the traversal and final tests read (triangle bounding spheres,
 // Moller-Trumbore edge layout).
 //
-// GB300 design: one thread per node.  Level-1 nodes read their B sorted rays
-// (consecutive, so a warp's loads cover one contiguous stretch of each SoA
-// array and stay in L1), fold the cone ray by ray (eqs. 1-4) and merge the
-// spheres (eqs. 7-8) as a balanced binary tree evaluated with a binary-counter
-// stack of log2(B) + 1 entries.  Upper levels merge B children the same way
-// (eqs. 5-8).  Every node is padded outward after its merge so the FP32
+// GB300 design: B consecutive lanes per node (32 / B nodes per warp).  Lane r
+// of a level-1 node loads sorted ray r (coalesced); the group's first lane
+// folds the cone ray by ray (eqs. 1-4) from shuffled directions, and the
+// spheres (eqs. 7-8) merge as a balanced binary tree of shuffle-downs.  Upper
+// levels merge their B children the same way (eqs. 5-8).  Every node is padded outward after its merge so the FP32
 // hierarchy contains its rays, and stores tan(spread), 1/cos(spread) for the
 // eq. 9 tests of the traversal.
 #include "common.cuh"
@@ -83,32 +82,33 @@ __device__ __forceinline__ void pad_node(SC& n, const Pads& p) {
     n.phi = fminf(PI_F, n.phi * (1.0f + p.cr) + p.ca);
 }
 
-// Balanced binary tree of merges in item order, evaluated as a binary counter:
-// equal-size neighbours on the stack merge (left operand = earlier items); at
-// the end the stack folds from the top.  Identical to merging item i with
-// item i + s at steps s = 1, 2, 4, ... whenever i + s exists.
+// Balanced binary tree of merges in item order: at steps s = 1, 2, 4, ...,
+// item i (a multiple of 2s) absorbs item i + s when it exists.  A node's items
+// sit in B consecutive lanes (B a power of two <= 32), so each step is one
+// shuffle-down within the lane group.
+__device__ __forceinline__ SC shfl_down_sc(const SC& v, unsigned s, int width) {
+    SC o;
+    o.c.x = __shfl_down_sync(FULL, v.c.x, s, width);
+    o.c.y = __shfl_down_sync(FULL, v.c.y, s, width);
+    o.c.z = __shfl_down_sync(FULL, v.c.z, s, width);
+    o.r = __shfl_down_sync(FULL, v.r, s, width);
+    o.x.x = __shfl_down_sync(FULL, v.x.x, s, width);
+    o.x.y = __shfl_down_sync(FULL, v.x.y, s, width);
+    o.x.z = __shfl_down_sync(FULL, v.x.z, s, width);
+    o.phi = __shfl_down_sync(FULL, v.phi, s, width);
+    return o;
+}
+
 template <bool CONES>
-struct TreeMerge {
-    SC st[7];
-    unsigned sz[7];
-    int top = 0;
-    __device__ __forceinline__ void merge_top() {
-        sphere_union(st[top - 2], st[top - 1]);
-        if (CONES) cone_union(st[top - 2], st[top - 1]);
-        sz[top - 2] += sz[top - 1];
-        --top;
+__device__ __forceinline__ void group_tree_merge(SC& item, unsigned r, unsigned m, unsigned B) {
+    for (unsigned s = 1; s < B; s <<= 1) {
+        const SC other = shfl_down_sc(item, s, (int)B);
+        if ((r & (2 * s - 1)) == 0 && r + s < m) {
+            sphere_union(item, other);
+            if (CONES) cone_union(item, other);
+        }
     }
-    __device__ __forceinline__ void push(const SC& v) {
-        st[top] = v;
-        sz[top] = 1;
-        ++top;
-        while (top >= 2 && sz[top - 1] == sz[top - 2]) merge_top();
-    }
-    __device__ __forceinline__ SC finish() {
-        while (top > 1) merge_top();
-        return st[0];
-    }
-};
+}
 
 struct LevelOut {
     float4* sphere;
@@ -143,6 +143,7 @@ struct Caps {
     unsigned v[CRSH_MAX_LEVELS];
 };
 
+// B lanes per node (B <= 32); 32 / B nodes per warp.
 __global__ void k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned B, unsigned L, Pads pads, LevelOut out,
                            unsigned* counts, Caps caps) {
     const unsigned n = *n_ptr;
@@ -160,23 +161,45 @@ __global__ void k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned B, unsig
         }
     }
     const unsigned lim = min(cnt, out.cap);
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < lim; j += gridDim.x * blockDim.x) {
-        const unsigned first = j * B, last = min(first + B, n);
-        f3 x = unit(mk3(rays.dx[first], rays.dy[first], rays.dz[first]));
-        float phi = 0.0f;
-        TreeMerge<false> tm;
-        for (unsigned i = first; i < last; ++i) {
-            if (i > first) cone_add_ray(x, phi, unit(mk3(rays.dx[i], rays.dy[i], rays.dz[i])));
-            SC leaf;
+    const unsigned lane = threadIdx.x & 31, r = lane & (B - 1), gbase = lane - r;
+    const unsigned groups_per_block = blockDim.x / B;
+    const unsigned gstart = blockIdx.x * groups_per_block + threadIdx.x / B;
+    const unsigned gstride = gridDim.x * groups_per_block;
+    // every lane of a warp runs the same number of iterations (shuffles below)
+    const unsigned iters = (lim + gstride - 1) / gstride;
+    for (unsigned it = 0; it < iters; ++it) {
+        const unsigned j = gstart + it * gstride;
+        const bool node_ok = j < lim;
+        const unsigned first = j * B;
+        const unsigned m = node_ok ? min(B, n - first) : 0u;
+        const bool mine = r < m;
+        const unsigned i = first + r;
+        f3 d = mk3(1.f, 0.f, 0.f);
+        SC leaf;
+        leaf.c = mk3(0.f, 0.f, 0.f);
+        leaf.r = 0.0f;
+        leaf.x = d;
+        leaf.phi = 0.0f;
+        if (mine) {
+            d = unit(mk3(rays.dx[i], rays.dy[i], rays.dz[i]));
             leaf.c = mk3(rays.ox[i], rays.oy[i], rays.oz[i]);
-            leaf.r = 0.0f;
-            tm.push(leaf);
         }
-        SC nd = tm.finish();
-        nd.x = x;
-        nd.phi = phi;
-        pad_node(nd, pads);
-        store_node(out, j, nd);
+        // cone: fold the rays in sorted order (eqs. 1-4), in the group's first lane
+        f3 x = d;
+        float phi = 0.0f;
+        for (unsigned k = 1; k < B; ++k) {
+            const f3 dk = mk3(__shfl_sync(FULL, d.x, gbase + k), __shfl_sync(FULL, d.y, gbase + k),
+                              __shfl_sync(FULL, d.z, gbase + k));
+            if (r == 0 && k < m) cone_add_ray(x, phi, dk);
+        }
+        // spheres: radius-0 leaves merged as a balanced tree (eqs. 7-8)
+        group_tree_merge<false>(leaf, r, m, B);
+        if (r == 0 && node_ok) {
+            leaf.x = x;
+            leaf.phi = phi;
+            pad_node(leaf, pads);
+            store_node(out, j, leaf);
+        }
     }
 }
 
@@ -184,21 +207,33 @@ __global__ void k_build_up(const float4* csph, const float4* ccone, const unsign
                            unsigned B, Pads pads, LevelOut out) {
     const unsigned below = counts[level_idx - 1];
     const unsigned cnt = counts[level_idx];
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += gridDim.x * blockDim.x) {
-        const unsigned first = j * B, last = min(first + B, below);
-        TreeMerge<true> tm;
-        for (unsigned i = first; i < last; ++i) {
-            float4 s = csph[i], c = ccone[i];
-            SC ch;
-            ch.c = mk3(s.x, s.y, s.z);
-            ch.r = s.w;
-            ch.x = mk3(c.x, c.y, c.z);
-            ch.phi = c.w;
-            tm.push(ch);
+    const unsigned lane = threadIdx.x & 31, r = lane & (B - 1);
+    const unsigned groups_per_block = blockDim.x / B;
+    const unsigned gstart = blockIdx.x * groups_per_block + threadIdx.x / B;
+    const unsigned gstride = gridDim.x * groups_per_block;
+    const unsigned iters = (cnt + gstride - 1) / gstride;
+    for (unsigned it = 0; it < iters; ++it) {
+        const unsigned j = gstart + it * gstride;
+        const bool node_ok = j < cnt;
+        const unsigned first = j * B;
+        const unsigned m = node_ok ? min(B, below - first) : 0u;
+        SC ch;
+        ch.c = mk3(0.f, 0.f, 0.f);
+        ch.r = 0.0f;
+        ch.x = mk3(1.f, 0.f, 0.f);
+        ch.phi = 0.0f;
+        if (r < m) {
+            const float4 sp = csph[first + r], co = ccone[first + r];
+            ch.c = mk3(sp.x, sp.y, sp.z);
+            ch.r = sp.w;
+            ch.x = mk3(co.x, co.y, co.z);
+            ch.phi = co.w;
         }
-        SC nd = tm.finish();
-        pad_node(nd, pads);
-        store_node(out, j, nd);
+        group_tree_merge<true>(ch, r, m, B);   // eqs. 5-8 in child order
+        if (r == 0 && node_ok) {
+            pad_node(ch, pads);
+            store_node(out, j, ch);
+        }
     }
 }
 
@@ -213,13 +248,14 @@ crsh_status build_launch(const crsh_rays* rays, const uint32_t* n_rays, const cr
     RaysIn ri{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz};
     LevelOut o1{reinterpret_cast<float4*>(h->sphere[0]), reinterpret_cast<float4*>(h->cone[0]),
                 reinterpret_cast<float2*>(h->trig[0]), h->capacity[0]};
-    const unsigned blocks1 = (h->capacity[0] + 127) / 128;
+    // B lanes per node: blocks of 128 threads hold 128 / B nodes
+    const unsigned blocks1 = (unsigned)(((size_t)h->capacity[0] * B + 127) / 128);
     const unsigned grid1 = blocks1 < (unsigned)dev.sms * 16 ? (blocks1 ? blocks1 : 1) : dev.sms * 16;
     k_build_l1<<<grid1, 128, 0, s>>>(ri, n_rays, B, L, pads, o1, h->count, caps);
     for (unsigned l = 1; l < L; ++l) {
         LevelOut o{reinterpret_cast<float4*>(h->sphere[l]), reinterpret_cast<float4*>(h->cone[l]),
                    reinterpret_cast<float2*>(h->trig[l]), h->capacity[l]};
-        const unsigned blocks = (h->capacity[l] + 127) / 128;
+        const unsigned blocks = (unsigned)(((size_t)h->capacity[l] * B + 127) / 128);
         const unsigned grid = blocks < (unsigned)dev.sms * 16 ? (blocks ? blocks : 1) : dev.sms * 16;
         k_build_up<<<grid, 128, 0, s>>>(reinterpret_cast<const float4*>(h->sphere[l - 1]),
                                         reinterpret_cast<const float4*>(h->cone[l - 1]), h->count, l, B, pads, o);

@@ -46,8 +46,8 @@ __device__ __forceinline__ bool mt_hit(float ox, float oy, float oz, float dx, f
     const float v = __uint_as_float(__float_as_uint(wn) ^ sgD ^ 0x80000000u);
     const float tp = __uint_as_float(__float_as_uint(tn) ^ sgD);
     const float ad = fabsf(dn);
-    const bool hit = (u >= 0.0f) & (v >= 0.0f) & (__fadd_rn(u, v) <= ad) & (tp > 0.0f) & (ad > 0.0f) &
-                     (tp <= __fmul_rn(tmax, ad));
+    // (|D| = 0 cannot pass: tp > 0 and tp <= t_max |D| exclude it, 0 * inf being NaN)
+    const bool hit = (u >= 0.0f) & (v >= 0.0f) & (__fadd_rn(u, v) <= ad) & (tp > 0.0f) & (tp <= __fmul_rn(tmax, ad));
     if (hit) t = __fdiv_rn(tp, ad);
     return hit && t > 0.0f && t <= tmax;
 }
@@ -64,59 +64,69 @@ struct RaysDev {
 
 constexpr int CH_WARPS = 4, CH_BLOCK = CH_WARPS * 32, CH_CHUNK = 512;
 
-// min over the 32/B lanes that hold the same ray, then one atomicMin per ray
-template <int B>
+// min over the lanes that hold the same ray (one per stream), then one
+// atomicMin per ray
+template <int H>
 __device__ __forceinline__ void flush_best(unsigned long long bk, bool rvalid, int sidx, unsigned ray,
                                            unsigned long long* best) {
 #pragma unroll
-    for (int o = B; o < 32; o <<= 1) {
+    for (int o = H; o < 32; o <<= 1) {
         const unsigned long long other = __shfl_xor_sync(FULL, bk, o);
         bk = other < bk ? other : bk;
     }
     if (rvalid && sidx == 0 && bk != NO_HIT) atomicMin(&best[ray], bk);
 }
 
+struct Ray7 {
+    float ox, oy, oz, dx, dy, dz, tmax;
+};
+
+__device__ __forceinline__ Ray7 load_ray(const RaysDev& rays, unsigned i) {
+    return Ray7{rays.ox[i], rays.oy[i], rays.oz[i], rays.dx[i], rays.dy[i], rays.dz[i], rays.tmax[i]};
+}
+
+// Each lane holds two rays of the current node (slots r and r + B/2); the
+// 32 / (B/2) streams of a warp walk every S-th staged triangle, so each
+// triangle record read from shared memory serves two tests.
 template <int B>
 __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, const uint32_t* ptri,
                                                       const unsigned* p_count, unsigned long long p_cap,
                                                       RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
                                                       unsigned long long* best, crsh_counters* ctr) {
-    constexpr int S = 32 / B;
+    constexpr int H = B / 2;            // lanes per node (two rays each)
+    constexpr int S = 32 / H;           // streams
     __shared__ float4 s_tri[CH_WARPS][32][3];
     __shared__ unsigned s_tid[CH_WARPS][32];
     const unsigned P = (unsigned)min((unsigned long long)*p_count, p_cap);
     const unsigned N = *n_ptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = lane % B, sidx = lane / B;
+    const int r = lane % H, sidx = lane / H;
     const unsigned gw = blockIdx.x * CH_WARPS + warp, nw = gridDim.x * CH_WARPS;
     unsigned long long n_tests = 0, n_hits = 0;
     for (unsigned q0 = gw * CH_CHUNK; q0 < P; q0 += nw * CH_CHUNK) {
         const unsigned q1 = min(q0 + CH_CHUNK, P);
-        unsigned cur = 0xffffffffu, ray = 0;
-        bool rvalid = false;
-        float ox = 0, oy = 0, oz = 0, dx = 0, dy = 0, dz = 0, tmax = 0;
-        unsigned long long bk = NO_HIT;
+        unsigned cur = 0xffffffffu, ray0 = 0, ray1 = 0;
+        bool v0 = false, v1 = false;
+        Ray7 a{0, 0, 0, 0, 0, 0, 0}, b{0, 0, 0, 0, 0, 0, 0};
+        unsigned long long k0 = NO_HIT, k1 = NO_HIT;
         unsigned q = q0;
         while (q < q1) {
             const unsigned node = pnode[q];   // same address in every lane
             if (node != cur) {
-                flush_best<B>(bk, rvalid, sidx, ray, best);
+                flush_best<H>(k0, v0, sidx, ray0, best);
+                flush_best<H>(k1, v1, sidx, ray1, best);
                 cur = node;
-                ray = node * B + r;
-                rvalid = ray < N;
-                if (rvalid) {
-                    ox = rays.ox[ray]; oy = rays.oy[ray]; oz = rays.oz[ray];
-                    dx = rays.dx[ray]; dy = rays.dy[ray]; dz = rays.dz[ray];
-                    tmax = rays.tmax[ray];
-                }
-                bk = NO_HIT;
+                ray0 = node * B + r;
+                ray1 = ray0 + H;
+                v0 = ray0 < N;
+                v1 = ray1 < N;
+                if (v0) a = load_ray(rays, ray0);
+                if (v1) b = load_ray(rays, ray1);
+                k0 = k1 = NO_HIT;
             }
-            // next group: up to 32 pairs of this node
             const unsigned g = min(32u, q1 - q);
             bool mine = false;
-            if ((unsigned)lane < g) {
-                mine = pnode[q + lane] == node;
-            }
+            if ((unsigned)lane < g) mine = pnode[q + lane] == node;
             const unsigned cnt = __popc(__ballot_sync(FULL, mine));   // a prefix: pairs are node-sorted
             if (mine) {
                 const unsigned tid = ptri[q + lane];
@@ -129,21 +139,27 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
             __syncwarp();
             const unsigned nrays = min((unsigned)B, N - node * B);
             if (lane == 0) n_tests += (unsigned long long)cnt * nrays;
-            if (rvalid) {
+            if (v0) {
                 for (unsigned j = sidx; j < cnt; j += S) {
+                    const float4 A = s_tri[warp][j][0], E1 = s_tri[warp][j][1], E2 = s_tri[warp][j][2];
                     float t;
-                    if (mt_hit(ox, oy, oz, dx, dy, dz, tmax, s_tri[warp][j][0], s_tri[warp][j][1],
-                               s_tri[warp][j][2], t)) {
+                    if (mt_hit(a.ox, a.oy, a.oz, a.dx, a.dy, a.dz, a.tmax, A, E1, E2, t)) {
                         ++n_hits;
                         const unsigned long long k = hit_key(t, s_tid[warp][j]);
-                        bk = k < bk ? k : bk;
+                        k0 = k < k0 ? k : k0;
+                    }
+                    if (v1 && mt_hit(b.ox, b.oy, b.oz, b.dx, b.dy, b.dz, b.tmax, A, E1, E2, t)) {
+                        ++n_hits;
+                        const unsigned long long k = hit_key(t, s_tid[warp][j]);
+                        k1 = k < k1 ? k : k1;
                     }
                 }
             }
             __syncwarp();
             q += cnt;
         }
-        flush_best<B>(bk, rvalid, sidx, ray, best);
+        flush_best<H>(k0, v0, sidx, ray0, best);
+        flush_best<H>(k1, v1, sidx, ray1, best);
     }
     n_tests = warp_sum64(n_tests);
     n_hits = warp_sum64(n_hits);

@@ -384,13 +384,19 @@ __device__ __forceinline__ void block_range(unsigned O, unsigned& w0, unsigned& 
     w1 = min(O, w0 + per);
 }
 
-// Accepted pairs per scan block (contiguous ranges of ballot words).
+// Accepted pairs per scan block (contiguous ranges of ballot words; ranges
+// start on multiples of SC_TILE words, so 16-byte loads are aligned).
 __global__ void __launch_bounds__(SC_BLOCK) k_reduce(StageBuf sb) {
     const unsigned O = sb.totals[1];
     unsigned w0, w1;
     block_range(O, w0, w1);
     unsigned c = 0;
-    for (unsigned w = w0 + threadIdx.x; w < w1; w += blockDim.x) c += __popc(sb.mask[w]);
+    const unsigned w1v = w0 + ((w1 - w0) & ~3u);
+    for (unsigned w = w0 + 4 * threadIdx.x; w < w1v; w += 4 * blockDim.x) {
+        const uint4 m = *reinterpret_cast<const uint4*>(sb.mask + w);
+        c += __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+    }
+    for (unsigned w = w1v + threadIdx.x; w < w1; w += blockDim.x) c += __popc(sb.mask[w]);
     c = __reduce_add_sync(FULL, c);
     __shared__ unsigned s_w[SC_BLOCK / 32];
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
@@ -435,11 +441,17 @@ __global__ void __launch_bounds__(SC_BLOCK) k_wordscan(StageBuf sb, PairOut out,
     for (unsigned t0 = w0; t0 < w1; t0 += SC_TILE) {
         const unsigned wb = t0 + threadIdx.x * SC_ITEMS;   // blocked: consecutive words per thread
         unsigned c[SC_ITEMS], sum = 0;
+        if (wb + SC_ITEMS <= w1) {   // aligned: wb is a multiple of 8 words
+            const uint4 a = *reinterpret_cast<const uint4*>(sb.mask + wb);
+            const uint4 b = *reinterpret_cast<const uint4*>(sb.mask + wb + 4);
+            c[0] = __popc(a.x); c[1] = __popc(a.y); c[2] = __popc(a.z); c[3] = __popc(a.w);
+            c[4] = __popc(b.x); c[5] = __popc(b.y); c[6] = __popc(b.z); c[7] = __popc(b.w);
+        } else {
 #pragma unroll
-        for (int i = 0; i < SC_ITEMS; ++i) {
-            c[i] = (wb + i < w1) ? __popc(sb.mask[wb + i]) : 0u;
-            sum += c[i];
+            for (int i = 0; i < SC_ITEMS; ++i) c[i] = (wb + i < w1) ? __popc(sb.mask[wb + i]) : 0u;
         }
+#pragma unroll
+        for (int i = 0; i < SC_ITEMS; ++i) sum += c[i];
         const unsigned inc = warp_incl_scan(sum);
         if (lane == 31) s_w[warp] = inc;
         __syncthreads();
@@ -450,10 +462,19 @@ __global__ void __launch_bounds__(SC_BLOCK) k_wordscan(StageBuf sb, PairOut out,
         }
         __syncthreads();
         unsigned long long r = run + s_w[warp] + inc - sum;
+        unsigned pv[SC_ITEMS];
 #pragma unroll
         for (int i = 0; i < SC_ITEMS; ++i) {
-            if (wb + i < w1) sb.pos[wb + i] = (unsigned)r;
+            pv[i] = (unsigned)r;
             r += c[i];
+        }
+        if (wb + SC_ITEMS <= w1) {
+            *reinterpret_cast<uint4*>(sb.pos + wb) = make_uint4(pv[0], pv[1], pv[2], pv[3]);
+            *reinterpret_cast<uint4*>(sb.pos + wb + 4) = make_uint4(pv[4], pv[5], pv[6], pv[7]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < SC_ITEMS; ++i)
+                if (wb + i < w1) sb.pos[wb + i] = pv[i];
         }
         run += s_w[SC_BLOCK / 32];
         __syncthreads();
@@ -501,22 +522,14 @@ __global__ void __launch_bounds__(256) k_emit(Parents par, StageBuf sb, PairOut 
                });
 }
 
-// Runs of a node-sorted pair list by binary search (the top level: few nodes).
-__global__ void k_runs_from_pairs(const uint32_t* node, const unsigned* p_count, const unsigned* n_count,
-                                  RunOut runs) {
-    const unsigned P = *p_count, Nn = *n_count;
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < Nn; k += gridDim.x * blockDim.x) {
-        unsigned b[2];
-        for (int e = 0; e < 2; ++e) {
-            unsigned lo = 0, hi = P;
-            while (lo < hi) {
-                const unsigned mid = (lo + hi) >> 1;
-                if (node[mid] < k + e) lo = mid + 1; else hi = mid;
-            }
-            b[e] = lo;
-        }
-        runs.start[k] = b[0];
-        runs.end[k] = b[1];
+// Runs of a node-sorted pair list: the pair that opens a node's run writes its
+// start, the pair that closes it writes its end (nodes without pairs keep 0, 0).
+__global__ void k_runs_from_pairs(const uint32_t* node, const unsigned* p_count, RunOut runs) {
+    const unsigned P = *p_count;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
+        const uint32_t n = node[q];
+        if (q == 0 || node[q - 1] != n) runs.start[n] = q;
+        if (q + 1 == P || node[q + 1] != n) runs.end[n] = q + 1;
     }
 }
 
@@ -635,7 +648,7 @@ template <class Parents>
 static void run_stage(const Parents& par, const TvWs& w, const float4* tsph, PairOut out, RunOut runs,
                       crsh_counters* ctr, int level_idx, unsigned B_paper, const DeviceInfo& dev, cudaStream_t s) {
     const unsigned warps_grid = dev.sms * 8;   // 256-thread blocks
-    const unsigned sg = std::min<unsigned>(SC_GRID_MAX, dev.sms * 2);
+    const unsigned sg = std::min<unsigned>(SC_GRID_MAX, dev.sms * 8);
     k_unit_scan<Parents><<<1, 1024, 0, s>>>(par, w.sb, ctr, level_idx, B_paper);
     k_count<Parents><<<warps_grid, 256, 0, s>>>(par, w.sb, tsph);
     k_reduce<<<sg, SC_BLOCK, 0, s>>>(w.sb);
@@ -676,9 +689,7 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     run_stage(top, w, tsph, pairs_of(L), w.runs[L - 1], ctr, (int)L - 1, 0u, dev, s);
     {
         const PairOut tp_out = pairs_of(L);
-        const unsigned blocks = (h->capacity[L - 1] + 255) / 256;
-        k_runs_from_pairs<<<std::min<unsigned>(blocks, dev.sms * 4), 256, 0, s>>>(tp_out.node, tp_out.count,
-                                                                                  h->count + (L - 1), w.runs[L - 1]);
+        k_runs_from_pairs<<<dev.sms * 4, 256, 0, s>>>(tp_out.node, tp_out.count, w.runs[L - 1]);
     }
     // levels L-1 .. 1: parents are the nodes of level l+1 and their pair runs
     for (unsigned l = L - 1; l >= 1; --l) {
