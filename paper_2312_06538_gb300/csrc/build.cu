@@ -2,11 +2,11 @@
 // data the traversal and final tests read (triangle bounding spheres,
 // Moller-Trumbore edge layout).
 //
-// GB300 design: B consecutive lanes per node (32 / B nodes per warp).  Lane r
-// of a level-1 node loads sorted ray r (coalesced); the group's first lane
-// folds the cone ray by ray (eqs. 1-4) from shuffled directions, and the
-// spheres (eqs. 7-8) merge as a balanced binary tree of shuffle-downs.  Upper
-// levels merge their B children the same way (eqs. 5-8).  Every node is padded outward after its merge so the FP32
+// GB300 design: a warp builds 32 level-1 nodes.  Rays are read coalesced,
+// the spheres (eqs. 7-8) merge as balanced binary trees of shuffle-downs
+// within B-lane groups, and the directions pass through shared memory so
+// that lane k folds node k's cone ray by ray (eqs. 1-4).  Upper levels merge
+// their B children in B-lane groups (eqs. 5-8).  Every node is padded outward after its merge so the FP32
 // hierarchy contains its rays, and stores tan(spread), 1/cos(spread) for the
 // eq. 9 tests of the traversal.
 #include "common.cuh"
@@ -128,9 +128,11 @@ __device__ __forceinline__ void store_node(const LevelOut& o, unsigned j, const 
         sincosf(n.phi, &sp, &cp);
         t = sp / cp;
         s = 1.0f / cp;
-        // round both up by a few ulps so the FP32 test stays conservative
-        t = t * (1.0f + 4.8e-7f);
-        s = s * (1.0f + 4.8e-7f);
+        // round both up by the rounding margin of the FP32 eq. 9 evaluation
+        // (a few ulps for tan/sec themselves, 2^-20 for the test's own sums
+        // and products), so the test in the traversal stays conservative
+        t = t * (1.0f + 1.5e-6f);
+        s = s * (1.0f + 1.5e-6f);
     }
     o.trig[j] = make_float2(t, s);
 }
@@ -143,9 +145,19 @@ struct Caps {
     unsigned v[CRSH_MAX_LEVELS];
 };
 
-// B lanes per node (B <= 32); 32 / B nodes per warp.
-__global__ void k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned B, unsigned L, Pads pads, LevelOut out,
-                           unsigned* counts, Caps caps) {
+// A warp builds 32 consecutive level-1 nodes.  The 32 B rays are read
+// coalesced (lane = ray), the spheres merge as shuffle trees within B-lane
+// groups, and the unit directions go to shared memory node-major; then lane k
+// folds node k's cone ray by ray (eqs. 1-4), so 32 sequential folds run side
+// by side.
+constexpr int BL1_WARPS = 2;
+__global__ void __launch_bounds__(BL1_WARPS * 32) k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned B,
+                                                              unsigned L, Pads pads, LevelOut out, unsigned* counts,
+                                                              Caps caps) {
+    // node k's ray i at k (B + 1) + i: an odd stride, so the fold's reads
+    // (lane = node) hit 32 distinct banks
+    __shared__ float s_dir[BL1_WARPS][3][32 * 33];
+    __shared__ float4 s_sph[BL1_WARPS][32];
     const unsigned n = *n_ptr;
     const unsigned cnt = (n + B - 1) / B;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -161,45 +173,56 @@ __global__ void k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned B, unsig
         }
     }
     const unsigned lim = min(cnt, out.cap);
-    const unsigned lane = threadIdx.x & 31, r = lane & (B - 1), gbase = lane - r;
-    const unsigned groups_per_block = blockDim.x / B;
-    const unsigned gstart = blockIdx.x * groups_per_block + threadIdx.x / B;
-    const unsigned gstride = gridDim.x * groups_per_block;
-    // every lane of a warp runs the same number of iterations (shuffles below)
-    const unsigned iters = (lim + gstride - 1) / gstride;
-    for (unsigned it = 0; it < iters; ++it) {
-        const unsigned j = gstart + it * gstride;
-        const bool node_ok = j < lim;
-        const unsigned first = j * B;
-        const unsigned m = node_ok ? min(B, n - first) : 0u;
-        const bool mine = r < m;
-        const unsigned i = first + r;
-        f3 d = mk3(1.f, 0.f, 0.f);
-        SC leaf;
-        leaf.c = mk3(0.f, 0.f, 0.f);
-        leaf.r = 0.0f;
-        leaf.x = d;
-        leaf.phi = 0.0f;
-        if (mine) {
-            d = unit(mk3(rays.dx[i], rays.dy[i], rays.dz[i]));
-            leaf.c = mk3(rays.ox[i], rays.oy[i], rays.oz[i]);
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, r = lane & (B - 1);
+    const unsigned stride = B + 1;
+    float* sdx = s_dir[warp][0];
+    float* sdy = s_dir[warp][1];
+    float* sdz = s_dir[warp][2];
+    const unsigned gw = blockIdx.x * BL1_WARPS + warp, nw = gridDim.x * BL1_WARPS;
+    for (unsigned j0 = gw * 32; j0 < lim; j0 += nw * 32) {
+        // load: B passes of 32 rays; pass t holds the 32 / B nodes from j0 + t (32 / B)
+        for (unsigned t = 0; t < B; ++t) {
+            const unsigned idx = t * 32 + lane;          // ray within this block of 32 nodes
+            const unsigned k = idx / B;                  // node within the block
+            const unsigned j = j0 + k;
+            const unsigned i = j0 * B + idx;             // sorted ray
+            const unsigned m = j < lim ? min(B, n - j * B) : 0u;
+            SC leaf;
+            leaf.c = mk3(0.f, 0.f, 0.f);
+            leaf.r = 0.0f;
+            leaf.x = mk3(1.f, 0.f, 0.f);
+            leaf.phi = 0.0f;
+            f3 d = mk3(1.f, 0.f, 0.f);
+            if (r < m) {
+                d = unit(mk3(rays.dx[i], rays.dy[i], rays.dz[i]));
+                leaf.c = mk3(rays.ox[i], rays.oy[i], rays.oz[i]);
+            }
+            sdx[k * stride + r] = d.x;
+            sdy[k * stride + r] = d.y;
+            sdz[k * stride + r] = d.z;
+            // spheres: radius-0 leaves merged as a balanced tree (eqs. 7-8)
+            group_tree_merge<false>(leaf, r, m, B);
+            if (r == 0) s_sph[warp][k] = make_float4(leaf.c.x, leaf.c.y, leaf.c.z, leaf.r);
         }
-        // cone: fold the rays in sorted order (eqs. 1-4), in the group's first lane
-        f3 x = d;
-        float phi = 0.0f;
-        for (unsigned k = 1; k < B; ++k) {
-            const f3 dk = mk3(__shfl_sync(FULL, d.x, gbase + k), __shfl_sync(FULL, d.y, gbase + k),
-                              __shfl_sync(FULL, d.z, gbase + k));
-            if (r == 0 && k < m) cone_add_ray(x, phi, dk);
+        __syncwarp();
+        // cone: lane k folds node j0 + k in sorted ray order (eqs. 1-4)
+        const unsigned j = j0 + lane;
+        if (j < lim) {
+            const unsigned m = min(B, n - j * B);
+            const unsigned base = lane * stride;
+            f3 x = mk3(sdx[base], sdy[base], sdz[base]);
+            float phi = 0.0f;
+            for (unsigned i = 1; i < m; ++i) cone_add_ray(x, phi, mk3(sdx[base + i], sdy[base + i], sdz[base + i]));
+            const float4 sp = s_sph[warp][lane];
+            SC node;
+            node.c = mk3(sp.x, sp.y, sp.z);
+            node.r = sp.w;
+            node.x = x;
+            node.phi = phi;
+            pad_node(node, pads);
+            store_node(out, j, node);
         }
-        // spheres: radius-0 leaves merged as a balanced tree (eqs. 7-8)
-        group_tree_merge<false>(leaf, r, m, B);
-        if (r == 0 && node_ok) {
-            leaf.x = x;
-            leaf.phi = phi;
-            pad_node(leaf, pads);
-            store_node(out, j, leaf);
-        }
+        __syncwarp();
     }
 }
 
@@ -249,9 +272,10 @@ crsh_status build_launch(const crsh_rays* rays, const uint32_t* n_rays, const cr
     LevelOut o1{reinterpret_cast<float4*>(h->sphere[0]), reinterpret_cast<float4*>(h->cone[0]),
                 reinterpret_cast<float2*>(h->trig[0]), h->capacity[0]};
     // B lanes per node: blocks of 128 threads hold 128 / B nodes
-    const unsigned blocks1 = (unsigned)(((size_t)h->capacity[0] * B + 127) / 128);
+    // a warp per 32 nodes
+    const unsigned blocks1 = (unsigned)(((size_t)h->capacity[0] + 32 * BL1_WARPS - 1) / (32 * BL1_WARPS));
     const unsigned grid1 = blocks1 < (unsigned)dev.sms * 16 ? (blocks1 ? blocks1 : 1) : dev.sms * 16;
-    k_build_l1<<<grid1, 128, 0, s>>>(ri, n_rays, B, L, pads, o1, h->count, caps);
+    k_build_l1<<<grid1, BL1_WARPS * 32, 0, s>>>(ri, n_rays, B, L, pads, o1, h->count, caps);
     for (unsigned l = 1; l < L; ++l) {
         LevelOut o{reinterpret_cast<float4*>(h->sphere[l]), reinterpret_cast<float4*>(h->cone[l]),
                    reinterpret_cast<float2*>(h->trig[l]), h->capacity[l]};

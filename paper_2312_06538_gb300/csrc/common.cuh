@@ -141,6 +141,11 @@ constexpr unsigned LB32_AGG = 1u << 30;
 constexpr unsigned LB32_INC = 2u << 30;
 constexpr unsigned LB32_VAL = (1u << 30) - 1;
 
+// The predecessors' words are read LB32_WIN at a time (independent loads in
+// flight), so a walk over many tiles that all hold only their own totals costs
+// one memory latency per LB32_WIN tiles.
+constexpr int LB32_WIN = 8;
+
 __device__ __forceinline__ unsigned lookback_thread32(unsigned* status, unsigned tile, unsigned stride,
                                                       unsigned aggregate, crsh_counters* ctr) {
     if (tile == 0) {
@@ -150,19 +155,33 @@ __device__ __forceinline__ unsigned lookback_thread32(unsigned* status, unsigned
     st_relaxed32(&status[(size_t)tile * stride], LB32_AGG | aggregate);
     unsigned excl = 0;
     unsigned spins = 0;
-    for (long long k = (long long)tile - 1; k >= 0; --k) {
-        unsigned s = ld_relaxed32(&status[(size_t)k * stride]);
-        while ((s >> 30) == 0) {
+    long long k = (long long)tile - 1;   // next predecessor to consume
+    while (k >= 0) {
+        unsigned s[LB32_WIN];
+#pragma unroll
+        for (int i = 0; i < LB32_WIN; ++i)
+            s[i] = (k - i >= 0) ? ld_relaxed32(&status[(size_t)(k - i) * stride]) : LB32_INC;
+        bool done = false;
+        int used = 0;
+#pragma unroll
+        for (int i = 0; i < LB32_WIN; ++i) {
+            if ((s[i] >> 30) == 0) break;          // not published yet: poll again from here
+            excl += s[i] & LB32_VAL;
+            used = i + 1;
+            if ((s[i] >> 30) == 2) {
+                done = true;
+                break;
+            }
+        }
+        if (done) break;
+        k -= used;
+        if (used == 0) {
             if (++spins > kSpinLimit) {
                 set_status(ctr, CRSH_ERR_TIMEOUT);
-                s = LB32_INC;
                 break;
             }
             __nanosleep(32);
-            s = ld_relaxed32(&status[(size_t)k * stride]);
         }
-        excl += s & LB32_VAL;
-        if ((s >> 30) == 2) break;
     }
     st_relaxed32(&status[(size_t)tile * stride], LB32_INC | (excl + aggregate));
     return excl;

@@ -14,6 +14,7 @@
 // of the winning triangle with the same test and scatters hits to the rays'
 // generation order.  Decisions (which triangle is closest) are FP32; the
 // reported (t, u, v) of the winner are recomputed in FP64 from the FP32 inputs.
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -62,7 +63,7 @@ struct RaysDev {
     const uint32_t* ray_id;
 };
 
-constexpr int CH_WARPS = 4, CH_BLOCK = CH_WARPS * 32, CH_CHUNK = 512;
+constexpr int CH_WARPS = 4, CH_BLOCK = CH_WARPS * 32;
 
 // min over the lanes that hold the same ray (one per stream), then one
 // atomicMin per ray
@@ -85,38 +86,141 @@ __device__ __forceinline__ Ray7 load_ray(const RaysDev& rays, unsigned i) {
     return Ray7{rays.ox[i], rays.oy[i], rays.oz[i], rays.dx[i], rays.dy[i], rays.dz[i], rays.tmax[i]};
 }
 
-// Each lane holds two rays of the current node (slots r and r + B/2); the
-// 32 / (B/2) streams of a warp walk every S-th staged triangle, so each
-// triangle record read from shared memory serves two tests.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+constexpr unsigned CH_PAIRS = 256;   // pairs per work chunk
+
+// Warps take chunks of CH_PAIRS consecutive pairs of the node-sorted pair
+// list from an atomic counter (the cost of a chunk depends on how many nodes
+// it spans) and walk them in groups: up to 32 consecutive pairs of one node.
+// Each lane holds two rays of the node (slots r and r + B/2); the 32 / (B/2)
+// streams of the warp walk every S-th triangle of the group, so each triangle
+// record read from shared memory serves two tests.  Software pipeline: while
+// group g is tested, the records of group g+1 are copied into the other
+// shared buffer (cp.async), the pair window of group g+2 is loaded into
+// registers and the chunk after the current one is already claimed, so the
+// chain counter -> pair -> triangle -> record never stalls the tests.
+// *work must be 0 at launch.
 template <int B>
 __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, const uint32_t* ptri,
                                                       const unsigned* p_count, unsigned long long p_cap,
                                                       RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
-                                                      unsigned long long* best, crsh_counters* ctr) {
+                                                      unsigned long long* best, unsigned* work, crsh_counters* ctr) {
     constexpr int H = B / 2;            // lanes per node (two rays each)
     constexpr int S = 32 / H;           // streams
-    __shared__ float4 s_tri[CH_WARPS][32][3];
-    __shared__ unsigned s_tid[CH_WARPS][32];
+    __shared__ __align__(16) float4 s_tri[CH_WARPS][2][32][3];
+    __shared__ unsigned s_tid[CH_WARPS][2][32];
     const unsigned P = (unsigned)min((unsigned long long)*p_count, p_cap);
     const unsigned N = *n_ptr;
+    const unsigned n_chunks = (P + CH_PAIRS - 1) / CH_PAIRS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = lane % H, sidx = lane / H;
-    const unsigned gw = blockIdx.x * CH_WARPS + warp, nw = gridDim.x * CH_WARPS;
     unsigned long long n_tests = 0, n_hits = 0;
-    for (unsigned q0 = gw * CH_CHUNK; q0 < P; q0 += nw * CH_CHUNK) {
-        const unsigned q1 = min(q0 + CH_CHUNK, P);
-        unsigned cur = 0xffffffffu, ray0 = 0, ray1 = 0;
-        bool v0 = false, v1 = false;
+    // claims are issued by lane 0 and read (broadcast) one chunk later
+    unsigned claim = 0;
+    if (lane == 0) claim = atomicAdd(work, 1u);
+    const unsigned c_first = __shfl_sync(FULL, claim, 0);
+    if (c_first < n_chunks) {
+        if (lane == 0) claim = atomicAdd(work, 1u);
+        // pair window at q (chunk end e): lane i holds pair q + i (node ~0 past e)
+        auto window = [&](unsigned q, unsigned e, unsigned& pw, unsigned& pt) {
+            const bool in = q + lane < e;
+            pw = in ? pnode[q + lane] : 0xffffffffu;
+            pt = in ? ptri[q + lane] : 0u;
+        };
+        // position after a group of cnt pairs at (q, e); false when the work is done
+        auto advance = [&](unsigned& q, unsigned& e, unsigned cnt) -> bool {
+            q += cnt;
+            if (q < e) return true;
+            const unsigned c = __shfl_sync(FULL, claim, 0);
+            if (c >= n_chunks) return false;
+            if (lane == 0) claim = atomicAdd(work, 1u);
+            q = c * CH_PAIRS;
+            e = min(P, q + CH_PAIRS);
+            return true;
+        };
+        // records of a group's triangles into buffer b (one commit per call)
+        auto stage = [&](int b, unsigned cnt, unsigned pt) {
+            if ((unsigned)lane < cnt) {
+                const float4* m = tri_mt + 3 * (size_t)pt;
+                cp_async16(&s_tri[warp][b][lane][0], m);
+                cp_async16(&s_tri[warp][b][lane][1], m + 1);
+                cp_async16(&s_tri[warp][b][lane][2], m + 2);
+                s_tid[warp][b][lane] = pt;
+            }
+            cp_async_commit();
+        };
+        unsigned q1 = c_first * CH_PAIRS, e1 = min(P, q1 + CH_PAIRS);
+        unsigned pw1, pt1;
+        window(q1, e1, pw1, pt1);
+        unsigned cur = __shfl_sync(FULL, pw1, 0);
+        unsigned cnt = __popc(__ballot_sync(FULL, pw1 == cur));   // a prefix: pairs are node-sorted
+        stage(0, cnt, pt1);
+        bool has1 = advance(q1, e1, cnt);
+        if (has1) window(q1, e1, pw1, pt1);
+        unsigned ray0 = cur * B + r, ray1 = ray0 + H;
+        bool v0 = ray0 < N, v1 = ray1 < N;
         Ray7 a{0, 0, 0, 0, 0, 0, 0}, b{0, 0, 0, 0, 0, 0, 0};
+        if (v0) a = load_ray(rays, ray0);
+        if (v1) b = load_ray(rays, ray1);
         unsigned long long k0 = NO_HIT, k1 = NO_HIT;
-        unsigned q = q0;
-        while (q < q1) {
-            const unsigned node = pnode[q];   // same address in every lane
-            if (node != cur) {
+        int buf = 0;
+        for (;;) {
+            unsigned nnode = 0xffffffffu, ncnt = 0;
+            unsigned pw2 = 0xffffffffu, pt2 = 0;
+            bool has2 = false;
+            if (has1) {   // warp-uniform
+                nnode = __shfl_sync(FULL, pw1, 0);
+                ncnt = __popc(__ballot_sync(FULL, pw1 == nnode));
+                stage(buf ^ 1, ncnt, pt1);
+                has2 = advance(q1, e1, ncnt);
+                if (has2) window(q1, e1, pw2, pt2);
+                if (nnode != cur) {   // warm L1 with the next node's rays
+                    const unsigned nr = nnode * B + r;
+                    if (nr < N) {
+                        prefetch_l1(rays.ox + nr); prefetch_l1(rays.oy + nr); prefetch_l1(rays.oz + nr);
+                        prefetch_l1(rays.dx + nr); prefetch_l1(rays.dy + nr); prefetch_l1(rays.dz + nr);
+                        prefetch_l1(rays.tmax + nr);
+                    }
+                }
+            } else {
+                cp_async_commit();   // keeps "all but the newest group" meaning this group
+            }
+            cp_async_wait_prev();
+            __syncwarp();
+            const unsigned nrays = min((unsigned)B, N - cur * B);
+            if (lane == 0) n_tests += (unsigned long long)cnt * nrays;
+            if (v0) {
+                for (unsigned j = sidx; j < cnt; j += S) {
+                    const float4 A = s_tri[warp][buf][j][0], E1 = s_tri[warp][buf][j][1],
+                                 E2 = s_tri[warp][buf][j][2];
+                    float t;
+                    if (mt_hit(a.ox, a.oy, a.oz, a.dx, a.dy, a.dz, a.tmax, A, E1, E2, t)) {
+                        ++n_hits;
+                        const unsigned long long k = hit_key(t, s_tid[warp][buf][j]);
+                        k0 = k < k0 ? k : k0;
+                    }
+                    if (v1 && mt_hit(b.ox, b.oy, b.oz, b.dx, b.dy, b.dz, b.tmax, A, E1, E2, t)) {
+                        ++n_hits;
+                        const unsigned long long k = hit_key(t, s_tid[warp][buf][j]);
+                        k1 = k < k1 ? k : k1;
+                    }
+                }
+            }
+            __syncwarp();   // buffer buf is refilled two groups on
+            if (!has1) break;
+            if (nnode != cur) {
                 flush_best<H>(k0, v0, sidx, ray0, best);
                 flush_best<H>(k1, v1, sidx, ray1, best);
-                cur = node;
-                ray0 = node * B + r;
+                cur = nnode;
+                ray0 = cur * B + r;
                 ray1 = ray0 + H;
                 v0 = ray0 < N;
                 v1 = ray1 < N;
@@ -124,39 +228,11 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
                 if (v1) b = load_ray(rays, ray1);
                 k0 = k1 = NO_HIT;
             }
-            const unsigned g = min(32u, q1 - q);
-            bool mine = false;
-            if ((unsigned)lane < g) mine = pnode[q + lane] == node;
-            const unsigned cnt = __popc(__ballot_sync(FULL, mine));   // a prefix: pairs are node-sorted
-            if (mine) {
-                const unsigned tid = ptri[q + lane];
-                const float4* m = tri_mt + 3 * (size_t)tid;
-                s_tid[warp][lane] = tid;
-                s_tri[warp][lane][0] = m[0];
-                s_tri[warp][lane][1] = m[1];
-                s_tri[warp][lane][2] = m[2];
-            }
-            __syncwarp();
-            const unsigned nrays = min((unsigned)B, N - node * B);
-            if (lane == 0) n_tests += (unsigned long long)cnt * nrays;
-            if (v0) {
-                for (unsigned j = sidx; j < cnt; j += S) {
-                    const float4 A = s_tri[warp][j][0], E1 = s_tri[warp][j][1], E2 = s_tri[warp][j][2];
-                    float t;
-                    if (mt_hit(a.ox, a.oy, a.oz, a.dx, a.dy, a.dz, a.tmax, A, E1, E2, t)) {
-                        ++n_hits;
-                        const unsigned long long k = hit_key(t, s_tid[warp][j]);
-                        k0 = k < k0 ? k : k0;
-                    }
-                    if (v1 && mt_hit(b.ox, b.oy, b.oz, b.dx, b.dy, b.dz, b.tmax, A, E1, E2, t)) {
-                        ++n_hits;
-                        const unsigned long long k = hit_key(t, s_tid[warp][j]);
-                        k1 = k < k1 ? k : k1;
-                    }
-                }
-            }
-            __syncwarp();
-            q += cnt;
+            cnt = ncnt;
+            buf ^= 1;
+            has1 = has2;
+            pw1 = pw2;
+            pt1 = pt2;
         }
         flush_best<H>(k0, v0, sidx, ray0, best);
         flush_best<H>(k1, v1, sidx, ray1, best);
@@ -170,8 +246,9 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->final_tests_paper = (unsigned long long)P * B;
 }
 
-__global__ void k_fill_best(unsigned long long* best, const unsigned* n_ptr) {
+__global__ void k_fill_best(unsigned long long* best, const unsigned* n_ptr, unsigned* work) {
     const unsigned n = *n_ptr;
+    if (work && blockIdx.x == 0 && threadIdx.x == 0) *work = 0;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) best[i] = NO_HIT;
 }
 
@@ -260,26 +337,43 @@ static RaysDev rays_dev(const crsh_rays* r) {
     return RaysDev{r->ox, r->oy, r->oz, r->dx, r->dy, r->dz, r->tmax, r->ray_id};
 }
 
+// One wave of resident blocks: every warp owns an equal contiguous share of
+// the pairs, so a second partial wave would double the time.
+template <int B>
+static void launch_closest(const crsh_pairs* pairs, const RaysDev& rd, const uint32_t* n_rays, const float4* mt,
+                           unsigned long long* best, unsigned* work, crsh_counters* ctr, cudaStream_t s,
+                           const DeviceInfo& dev) {
+    static std::atomic<int> per_sm[64];   // resident blocks per SM, per device
+    const int d = (dev.device >= 0 && dev.device < 64) ? dev.device : 0;
+    int b = per_sm[d].load(std::memory_order_relaxed);
+    if (b <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_closest<B>, CH_BLOCK, 0) != cudaSuccess || b <= 0) b = 1;
+        per_sm[d].store(b, std::memory_order_relaxed);
+    }
+    k_closest<B><<<dev.sms * b, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd,
+                                                         n_rays, mt, best, work, ctr);
+}
+
 crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
                                const crsh_scene* sc, const crsh_pairs* pairs, crsh_hits* out, crsh_counters* ctr,
                                void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev) {
     if (ws_bytes < closest_hit_workspace(rays->capacity)) return CRSH_ERR_INVALID_ARG;
     unsigned long long* best = reinterpret_cast<unsigned long long*>(ws);
+    unsigned* work = reinterpret_cast<unsigned*>(best + rays->capacity);   // in the 256 spare bytes
     {
         char* c0 = reinterpret_cast<char*>(&ctr->final_tests);
         if (cudaMemsetAsync(c0, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) return CRSH_ERR_CUDA;
     }
     const unsigned fb = dev.sms * 8;
-    k_fill_best<<<fb, 256, 0, s>>>(best, n_rays);
-    const unsigned grid = dev.sms * 8;
+    k_fill_best<<<fb, 256, 0, s>>>(best, n_rays, work);
     const RaysDev rd = rays_dev(rays);
     const float4* mt = reinterpret_cast<const float4*>(sc->tri_mt);
     switch (h->bundle) {
-        case 2: k_closest<2><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
-        case 4: k_closest<4><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
-        case 8: k_closest<8><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
-        case 16: k_closest<16><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
-        case 32: k_closest<32><<<grid, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd, n_rays, mt, best, ctr); break;
+        case 2: launch_closest<2>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
+        case 4: launch_closest<4>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
+        case 8: launch_closest<8>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
+        case 16: launch_closest<16>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
+        case 32: launch_closest<32>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
         default: return CRSH_ERR_INVALID_ARG;
     }
     k_finalize<<<fb, 256, 0, s>>>(rd, n_rays, *sc, best, *out);

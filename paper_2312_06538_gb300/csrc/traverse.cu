@@ -25,20 +25,20 @@ constexpr int TV_BLOCK = 256, TV_ITEMS = 4, TV_TILE = TV_BLOCK * TV_ITEMS;
 static_assert(TV_ITEMS * (TV_BLOCK / 32) == 32, "one warp scans the per-warp counts");
 
 // eq. 9 in FP32.  C = node sphere centre (cone apex), d = node radius, x =
-// unit axis, tan/sec of the spread precomputed (sec = +inf: accept all);
-// (P, r) = tested sphere.  Accept iff |s| tan + (d + r) sec >= |P - H| with
-// s = (P - C).x and H = C + s x, compared squared, with the left side raised
-// by 2^-20 (node and triangle radii already carry the coordinate-scaled
-// rounding margins).
+// unit axis, T/S = tan/sec of the spread (precomputed, rounded up by the
+// rounding margin of this evaluation; both +inf for a node that accepts
+// everything); (P, r) = tested sphere.  Accept iff |s| T + (d + r) S >= |P - H|
+// with s = (P - C).x and H = C + s x, compared squared and written as
+// !(lhs^2 < |P - H|^2) so that a NaN (0 * inf on an accept-all node) accepts.
+// Branch-free; node and triangle radii already carry the coordinate-scaled
+// rounding margins.
 __device__ __forceinline__ bool eq9(float4 sph, float4 cone, float2 trig, float4 P) {
-    if (trig.y == __int_as_float(0x7f800000)) return true;
     const float vx = P.x - sph.x, vy = P.y - sph.y, vz = P.z - sph.z;
     const float s = vx * cone.x + vy * cone.y + vz * cone.z;
     const float wx = vx - s * cone.x, wy = vy - s * cone.y, wz = vz - s * cone.z;
     const float w2 = wx * wx + wy * wy + wz * wz;
-    float lhs = fabsf(s) * trig.x + (sph.w + P.w) * trig.y;
-    lhs *= 1.00000095f;
-    return lhs * lhs >= w2;
+    const float lhs = fmaf(fabsf(s), trig.x, (sph.w + P.w) * trig.y);
+    return !(lhs * lhs < w2);
 }
 
 struct Node3 {
@@ -352,7 +352,39 @@ __device__ __forceinline__ void warp_unit_range(unsigned U, unsigned& u0, unsign
     u1 = min(U, u0 + per);
 }
 
+// Position in the unit list: the parent p owning the current unit, its
+// triangle run [s, s + len), its first unit ub and first ballot word ob.
+template <class Parents>
+struct UnitCursor {
+    unsigned p, next, s, len, ub, ob;
+    __device__ __forceinline__ void enter(const Parents& par, const StageBuf& sb) {
+        next = sb.ubase[p + 1];
+        ub = sb.ubase[p];
+        ob = sb.obase[p];
+        par.range(p, s, len);
+    }
+    __device__ __forceinline__ void start(const Parents& par, const StageBuf& sb, unsigned u) {
+        p = find_parent(sb.ubase, par.count(), u);
+        enter(par, sb);
+    }
+    // u must be below the unit total (parents without triangles own no units)
+    __device__ __forceinline__ void seek(const Parents& par, const StageBuf& sb, unsigned u) {
+        while (u >= next) {
+            ++p;
+            enter(par, sb);
+        }
+    }
+    // this lane's triangle of unit u (0 when past the parent's run)
+    __device__ __forceinline__ unsigned tri(const Parents& par, unsigned u, bool& valid) const {
+        const unsigned j = ((u - ub) << 5) + (threadIdx.x & 31);
+        valid = j < len;
+        return valid ? par.tri(s, j) : 0u;
+    }
+};
+
 // Count pass: one 32-bit ballot per (child, chunk): eq. 9 for 32 triangles.
+// Software-pipelined over the warp's units: the triangle index of unit u+2
+// and the triangle sphere of unit u+1 are in flight while unit u is tested.
 template <class Parents>
 __global__ void __launch_bounds__(256) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
     const unsigned U = sb.totals[0];
@@ -360,20 +392,50 @@ __global__ void __launch_bounds__(256) k_count(Parents par, StageBuf sb, const f
     warp_unit_range(U, u0, u1);
     if (u0 >= u1) return;
     const int lane = threadIdx.x & 31;
-    walk_units(par, sb, u0, u1,
-               [&](unsigned p, unsigned s, unsigned, unsigned nch, unsigned nc, unsigned ob, unsigned ch, unsigned j,
-                   bool valid) {
-                   float4 ts = make_float4(0.f, 0.f, 0.f, 0.f);
-                   if (valid) ts = tri_sphere[par.tri(s, j)];
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    UnitCursor<Parents> c0, c1;
+    c0.start(par, sb, u0);
+    bool v0, v1 = false;
+    float4 ts0 = zero;
+    {
+        const unsigned t0 = c0.tri(par, u0, v0);
+        if (v0) ts0 = tri_sphere[t0];
+    }
+    unsigned t1 = 0;
+    c1 = c0;
+    if (u0 + 1 < u1) {
+        c1.seek(par, sb, u0 + 1);
+        t1 = c1.tri(par, u0 + 1, v1);
+    }
+    for (unsigned u = u0; u < u1; ++u) {
+        float4 ts1 = zero;
+        if (v1) ts1 = tri_sphere[t1];
+        UnitCursor<Parents> c2 = c1;
+        bool v2 = false;
+        unsigned t2 = 0;
+        if (u + 2 < u1) {
+            c2.seek(par, sb, u + 2);
+            t2 = c2.tri(par, u + 2, v2);
+        }
+        const unsigned nch = (c0.len + 31) >> 5, nc = par.nchild(c0.p);
+        const unsigned a0 = par.child_id(c0.p, 0);
+        const float4* csp = par.child.sphere + a0;
+        const float4* cco = par.child.cone + a0;
+        const float2* ctg = par.child.trig + a0;
+        unsigned* mw = sb.mask + c0.ob + (u - c0.ub);
 #pragma unroll 4
-                   for (unsigned c = 0; c < nc; ++c) {
-                       const unsigned a = par.child_id(p, c);
-                       const bool ok =
-                           valid && eq9(par.child.sphere[a], par.child.cone[a], par.child.trig[a], ts);
-                       const unsigned m = __ballot_sync(FULL, ok);
-                       if (lane == 0) sb.mask[ob + c * nch + ch] = m;
-                   }
-               });
+        for (unsigned c = 0; c < nc; ++c) {
+            const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
+            const unsigned m = __ballot_sync(FULL, ok);
+            if (lane == 0) mw[c * nch] = m;
+        }
+        c0 = c1;
+        v0 = v1;
+        ts0 = ts1;
+        c1 = c2;
+        v1 = v2;
+        t1 = t2;
+    }
 }
 
 constexpr int SC_BLOCK = 256, SC_ITEMS = 8, SC_TILE = SC_BLOCK * SC_ITEMS, SC_GRID_MAX = 2048;
