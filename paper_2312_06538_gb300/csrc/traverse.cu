@@ -15,6 +15,7 @@
 // The emit pass also records each child's run [start, end) of the output,
 // which is how the next level finds a parent's triangles.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -181,6 +182,7 @@ struct MeshOp {
 // ---------------------------------------------------------------------------
 
 struct LevelParents {           // parents: nodes of level l+1, pair runs [start, end)
+    static constexpr bool kChunkCull = true;   // B children per parent: pre-test chunk spheres
     const uint32_t* ptri;
     const unsigned* pstart;
     const unsigned* pend;
@@ -205,6 +207,7 @@ struct LevelParents {           // parents: nodes of level l+1, pair runs [start
 };
 
 struct TopParents {             // parents: accepted (top node, mesh) pairs, grouped by node
+    static constexpr bool kChunkCull = false;  // one child per parent: nothing to share
     const uint32_t* mp_node;
     const uint32_t* mp_mesh;
     const unsigned* a_count;
@@ -232,6 +235,7 @@ struct StageBuf {
     unsigned* mask;             // ballot words in output order (parent, child, chunk)
     unsigned* pos;              // exclusive prefix of the ballot popcounts (O + 1 entries)
     unsigned* bsum;             // per scan block: accepted pairs
+    unsigned* work;             // [0] count pass, [1] emit pass: claimed unit batches (zeroed per call)
 };
 
 // Pair runs of the level a stage writes: [start[n], end[n]) for node n
@@ -316,42 +320,6 @@ __device__ __forceinline__ unsigned find_parent(const unsigned* base, unsigned n
     return lo;
 }
 
-// Walks the units [u0, u1) of a warp in order (parent by parent) and calls
-// body(p, s, len, nch, nc, ob, ch, j, valid) for each unit; warp-uniform.
-template <class Parents, class Body>
-__device__ __forceinline__ void walk_units(const Parents& par, const StageBuf& sb, unsigned u0, unsigned u1,
-                                           Body body) {
-    const int lane = threadIdx.x & 31;
-    const unsigned n = par.count();
-    unsigned p = find_parent(sb.ubase, n, u0);
-    unsigned next = sb.ubase[p + 1];
-    unsigned s, len;
-    par.range(p, s, len);
-    unsigned nch = (len + 31) >> 5, nc = par.nchild(p), ob = sb.obase[p], ub = sb.ubase[p];
-    for (unsigned u = u0; u < u1; ++u) {
-        while (u >= next) {   // parents without triangles own no units
-            ++p;
-            next = sb.ubase[p + 1];
-            par.range(p, s, len);
-            nch = (len + 31) >> 5;
-            nc = par.nchild(p);
-            ob = sb.obase[p];
-            ub = sb.ubase[p];
-        }
-        const unsigned ch = u - ub;
-        const unsigned j = (ch << 5) + lane;
-        body(p, s, len, nch, nc, ob, ch, j, j < len);
-    }
-}
-
-__device__ __forceinline__ void warp_unit_range(unsigned U, unsigned& u0, unsigned& u1) {
-    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
-    const unsigned per = (U + nw - 1) / nw;
-    u0 = min(U, gw * per);
-    u1 = min(U, u0 + per);
-}
-
 // Position in the unit list: the parent p owning the current unit, its
 // triangle run [s, s + len), its first unit ub and first ballot word ob.
 template <class Parents>
@@ -382,57 +350,157 @@ struct UnitCursor {
     }
 };
 
+// Work split of a count or emit pass.  With at least dyn_min units per warp
+// the units are handed out in batches from an atomic counter (the cost of a
+// unit depends on how many children accept it), about four batches per warp
+// and at most UNIT_BATCH units each; a warp claims the batch after the
+// current one when it starts a batch, so the claim's latency is hidden.  With
+// fewer, each warp takes one contiguous range (no atomics: at a few units per
+// warp the claims themselves would dominate).  The position (cursor, unit u,
+// batch end e) advances one unit at a time.  All calls are warp-uniform.
+constexpr unsigned UNIT_BATCH = 16;
+
+struct WorkSplit {
+    unsigned U, nw, per, batch;   // per = 0: claimed batches; else the static range length
+    unsigned* work;
+    __device__ __forceinline__ WorkSplit(unsigned U_, unsigned* work_, unsigned dyn_min) : U(U_), work(work_) {
+        nw = gridDim.x * (blockDim.x >> 5);
+        per = (U >= dyn_min * nw) ? 0u : (U + nw - 1) / nw;
+        batch = max(1u, min(UNIT_BATCH, U / (4u * nw)));
+    }
+    // first claim: the warp's own index for a static split
+    __device__ __forceinline__ unsigned first_claim() const {
+        if (per) return (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        return ((threadIdx.x & 31) == 0) ? atomicAdd(work, 1u) : 0u;
+    }
+};
+
+template <class Parents>
+struct UnitStream {
+    UnitCursor<Parents> c;
+    unsigned u, e;
+    __device__ __forceinline__ bool take(const Parents& par, const StageBuf& sb, const WorkSplit& ws,
+                                         unsigned& claim) {
+        const unsigned b = __shfl_sync(FULL, claim, 0);
+        if (ws.per) {
+            if (b >= ws.nw) return false;
+            u = b * ws.per;
+            if (u >= ws.U) return false;
+            e = min(ws.U, u + ws.per);
+            claim = ws.nw;   // one range per warp
+        } else {
+            if (b >= (ws.U + ws.batch - 1) / ws.batch) return false;
+            if ((threadIdx.x & 31) == 0) claim = atomicAdd(ws.work, 1u);
+            u = b * ws.batch;
+            e = min(ws.U, u + ws.batch);
+        }
+        c.start(par, sb, u);
+        return true;
+    }
+    __device__ __forceinline__ bool step(const Parents& par, const StageBuf& sb, const WorkSplit& ws,
+                                         unsigned& claim) {
+        if (u + 1 < e) {
+            ++u;
+            c.seek(par, sb, u);
+            return true;
+        }
+        return take(par, sb, ws, claim);
+    }
+};
+
+// Bounding sphere of the chunk's triangle spheres (warp-uniform): centre the
+// mean of the valid lanes' centres, radius the largest |c_i - K| + r_i, padded
+// outward like a triangle sphere (FP32 rounding of this radius and of the
+// eq. 9 evaluation), so the exact sphere contains every triangle sphere.
+__device__ __forceinline__ float4 chunk_sphere(float4 ts, bool valid) {
+    const unsigned nv = __popc(__ballot_sync(FULL, valid));
+    float sx = valid ? ts.x : 0.f, sy = valid ? ts.y : 0.f, sz = valid ? ts.z : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(FULL, sx, o);
+        sy += __shfl_xor_sync(FULL, sy, o);
+        sz += __shfl_xor_sync(FULL, sz, o);
+    }
+    const float inv = 1.0f / (float)nv;
+    const float kx = sx * inv, ky = sy * inv, kz = sz * inv;
+    const float dx = ts.x - kx, dy = ts.y - ky, dz = ts.z - kz;
+    float R = valid ? sqrtf(dx * dx + dy * dy + dz * dz) + ts.w : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(FULL, R, o));
+    const float mag = fabsf(kx) + fabsf(ky) + fabsf(kz) + R;
+    R = R * (1.0f + 9.6e-7f) + 3.9e-6f * mag;
+    return make_float4(kx, ky, kz, R);
+}
+
 // Count pass: one 32-bit ballot per (child, chunk): eq. 9 for 32 triangles.
 // Software-pipelined over the warp's units: the triangle index of unit u+2
 // and the triangle sphere of unit u+1 are in flight while unit u is tested.
+// Below the top level, lane c first tests child c against the chunk's
+// bounding sphere: eq. 9 is an exact sphere-against-region test, so a child
+// that rejects the bounding sphere rejects every triangle sphere inside it
+// (its word is 0) and only the children that accept it run the 32-lane tests.
 template <class Parents>
-__global__ void __launch_bounds__(256) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
-    const unsigned U = sb.totals[0];
-    unsigned u0, u1;
-    warp_unit_range(U, u0, u1);
-    if (u0 >= u1) return;
+__global__ void __launch_bounds__(256, 5) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
+    const WorkSplit ws(sb.totals[0], sb.work + 0, 16u);
     const int lane = threadIdx.x & 31;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    UnitCursor<Parents> c0, c1;
-    c0.start(par, sb, u0);
+    unsigned claim = ws.first_claim();
+    UnitStream<Parents> p0;
+    if (!p0.take(par, sb, ws, claim)) return;
     bool v0, v1 = false;
     float4 ts0 = zero;
     {
-        const unsigned t0 = c0.tri(par, u0, v0);
+        const unsigned t0 = p0.c.tri(par, p0.u, v0);
         if (v0) ts0 = tri_sphere[t0];
     }
+    UnitStream<Parents> p1 = p0;
+    bool has1 = p1.step(par, sb, ws, claim);
     unsigned t1 = 0;
-    c1 = c0;
-    if (u0 + 1 < u1) {
-        c1.seek(par, sb, u0 + 1);
-        t1 = c1.tri(par, u0 + 1, v1);
-    }
-    for (unsigned u = u0; u < u1; ++u) {
+    if (has1) t1 = p1.c.tri(par, p1.u, v1);
+    for (;;) {
         float4 ts1 = zero;
         if (v1) ts1 = tri_sphere[t1];
-        UnitCursor<Parents> c2 = c1;
-        bool v2 = false;
+        UnitStream<Parents> p2 = p1;
+        bool has2 = false, v2 = false;
         unsigned t2 = 0;
-        if (u + 2 < u1) {
-            c2.seek(par, sb, u + 2);
-            t2 = c2.tri(par, u + 2, v2);
+        if (has1) {
+            has2 = p2.step(par, sb, ws, claim);
+            if (has2) t2 = p2.c.tri(par, p2.u, v2);
         }
+        const UnitCursor<Parents>& c0 = p0.c;
         const unsigned nch = (c0.len + 31) >> 5, nc = par.nchild(c0.p);
         const unsigned a0 = par.child_id(c0.p, 0);
         const float4* csp = par.child.sphere + a0;
         const float4* cco = par.child.cone + a0;
         const float2* ctg = par.child.trig + a0;
-        unsigned* mw = sb.mask + c0.ob + (u - c0.ub);
+        unsigned* mw = sb.mask + c0.ob + (p0.u - c0.ub);
+        if (Parents::kChunkCull) {
+            const float4 K = chunk_sphere(ts0, v0);
+            const bool mine = (unsigned)lane < nc;
+            const bool acc = mine && eq9(csp[lane], cco[lane], ctg[lane], K);
+            if (mine && !acc) mw[lane * nch] = 0u;
+            unsigned todo = __ballot_sync(FULL, acc);
+            while (todo) {
+                const unsigned c = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
+                const unsigned m = __ballot_sync(FULL, ok);
+                if (lane == 0) mw[c * nch] = m;
+            }
+        } else {
 #pragma unroll 4
-        for (unsigned c = 0; c < nc; ++c) {
-            const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
-            const unsigned m = __ballot_sync(FULL, ok);
-            if (lane == 0) mw[c * nch] = m;
+            for (unsigned c = 0; c < nc; ++c) {
+                const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
+                const unsigned m = __ballot_sync(FULL, ok);
+                if (lane == 0) mw[c * nch] = m;
+            }
         }
-        c0 = c1;
+        if (!has1) break;
+        p0 = p1;
         v0 = v1;
         ts0 = ts1;
-        c1 = c2;
+        p1 = p2;
+        has1 = has2;
         v1 = v2;
         t1 = t2;
     }
@@ -545,43 +613,66 @@ __global__ void __launch_bounds__(SC_BLOCK) k_wordscan(StageBuf sb, PairOut out,
 
 // Emit pass: the count pass's walk again; each set ballot bit becomes a
 // (child, triangle) pair at pos[word] + rank.  Unit (p, 0) also records the
-// children's runs [start, end).
+// children's runs [start, end).  The triangle index and the children's words
+// of the next unit are loaded while the current unit is written.
+template <class Parents>
+struct EmitLoads {
+    unsigned t, mc, pc, pe;   // triangle; child `lane`'s mask and position; its run end (first chunk)
+    __device__ __forceinline__ void load(const Parents& par, const StageBuf& sb, const UnitStream<Parents>& q) {
+        const int lane = threadIdx.x & 31;
+        bool valid;
+        t = q.c.tri(par, q.u, valid);
+        const unsigned nch = (q.c.len + 31) >> 5, nc = par.nchild(q.c.p), ch = q.u - q.c.ub;
+        mc = pc = pe = 0;
+        if ((unsigned)lane < nc) {
+            const unsigned w = q.c.ob + lane * nch + ch;
+            mc = sb.mask[w];
+            pc = sb.pos[w];
+            if (ch == 0) pe = sb.pos[q.c.ob + (lane + 1) * nch];
+        }
+    }
+};
+
 template <class Parents>
 __global__ void __launch_bounds__(256) k_emit(Parents par, StageBuf sb, PairOut out, RunOut runs) {
-    const unsigned U = sb.totals[0];
-    unsigned u0, u1;
-    warp_unit_range(U, u0, u1);
-    if (u0 >= u1) return;
+    const WorkSplit ws(sb.totals[0], sb.work + 1, 32u);
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-    walk_units(par, sb, u0, u1,
-               [&](unsigned p, unsigned s, unsigned, unsigned nch, unsigned nc, unsigned ob, unsigned ch, unsigned j,
-                   bool valid) {
-                   const unsigned t = valid ? par.tri(s, j) : 0u;
-                   // lane c fetches child c's ballot and output position (all in flight at once)
-                   unsigned mc = 0, pc = 0;
-                   if ((unsigned)lane < nc) {
-                       const unsigned w = ob + lane * nch + ch;
-                       mc = sb.mask[w];
-                       pc = sb.pos[w];
-                   }
-                   unsigned any = __ballot_sync(FULL, mc != 0);
-                   while (any) {
-                       const int c = __ffs(any) - 1;
-                       any &= any - 1;
-                       const unsigned m = __shfl_sync(FULL, mc, c);
-                       const unsigned base = __shfl_sync(FULL, pc, c);
-                       if ((m >> lane) & 1u) store_pair(out, base + __popc(m & lt), par.child_id(p, c), t);
-                   }
-                   if (ch == 0 && (unsigned)lane < nc) {
-                       // runs index the written list: clamp to its capacity (a list
-                       // that overflowed is truncated and flagged CRSH_ERR_CAPACITY)
-                       const unsigned c = lane, a = par.child_id(p, c);
-                       if (par.first_of_child(p, c)) runs.start[a] = (unsigned)min((unsigned long long)pc, out.cap);
-                       if (par.last_of_child(p, c))
-                           runs.end[a] = (unsigned)min((unsigned long long)sb.pos[ob + (c + 1) * nch], out.cap);
-                   }
-               });
+    unsigned claim = ws.first_claim();
+    UnitStream<Parents> p0;
+    if (!p0.take(par, sb, ws, claim)) return;
+    EmitLoads<Parents> l0, l1;
+    l0.load(par, sb, p0);
+    UnitStream<Parents> p1 = p0;
+    bool has1 = p1.step(par, sb, ws, claim);
+    for (;;) {
+        if (has1) l1.load(par, sb, p1);
+        UnitStream<Parents> p2 = p1;
+        bool has2 = false;
+        if (has1) has2 = p2.step(par, sb, ws, claim);
+        const UnitCursor<Parents>& c0 = p0.c;
+        const unsigned nc = par.nchild(c0.p), ch = p0.u - c0.ub;
+        unsigned any = __ballot_sync(FULL, l0.mc != 0);
+        while (any) {
+            const int c = __ffs(any) - 1;
+            any &= any - 1;
+            const unsigned m = __shfl_sync(FULL, l0.mc, c);
+            const unsigned base = __shfl_sync(FULL, l0.pc, c);
+            if ((m >> lane) & 1u) store_pair(out, base + __popc(m & lt), par.child_id(c0.p, c), l0.t);
+        }
+        if (ch == 0 && (unsigned)lane < nc) {
+            // runs index the written list: clamp to its capacity (a list
+            // that overflowed is truncated and flagged CRSH_ERR_CAPACITY)
+            const unsigned a = par.child_id(c0.p, lane);
+            if (par.first_of_child(c0.p, lane)) runs.start[a] = (unsigned)min((unsigned long long)l0.pc, out.cap);
+            if (par.last_of_child(c0.p, lane)) runs.end[a] = (unsigned)min((unsigned long long)l0.pe, out.cap);
+        }
+        if (!has1) break;
+        p0 = p1;
+        l0 = l1;
+        p1 = p2;
+        has1 = has2;
+    }
 }
 
 // Runs of a node-sorted pair list: the pair that opens a node's run writes its
@@ -650,6 +741,7 @@ struct TvWs {
     char* ctl;                           // zeroed per call: counts, counters, runs
     size_t ctl_bytes;
     unsigned* counts;                    // [0] mesh pairs, [1 + l] pairs of level l+1
+    unsigned* work;                      // 2 per stage (count, emit): claimed unit batches
     unsigned* tile_ctr;
     unsigned long long* st_mesh;
     size_t total;
@@ -683,6 +775,7 @@ TvWs carve_tv(void* ws, const crsh_hierarchy* h, uint32_t n_tris, uint32_t n_mes
     c.off = (c.off + 255) & ~size_t(255);
     const size_t ctl0 = c.off;
     w.counts = c.take<unsigned>(CRSH_MAX_LEVELS + 2);
+    w.work = c.take<unsigned>(2 * (CRSH_MAX_LEVELS + 1));
     w.tile_ctr = c.take<unsigned>(4);
     w.st_mesh = c.take<unsigned long long>(mp / TV_TILE + 2);
     for (unsigned l = 0; l < L; ++l) {
@@ -706,16 +799,35 @@ size_t traverse_workspace(const crsh_hierarchy* h, uint32_t n_tris, uint32_t n_m
     return carve_tv(nullptr, h, n_tris, n_meshes, cap).total;
 }
 
+// Blocks of a kernel resident on one SM (cached per kernel and device).
+template <class K>
+static unsigned resident_blocks(K kernel, int block, const DeviceInfo& dev) {
+    static std::atomic<int> per_sm[64];
+    const int d = (dev.device >= 0 && dev.device < 64) ? dev.device : 0;
+    int b = per_sm[d].load(std::memory_order_relaxed);
+    if (b <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, 0) != cudaSuccess || b <= 0) b = 1;
+        per_sm[d].store(b, std::memory_order_relaxed);
+    }
+    return (unsigned)b;
+}
+
+// stage: 0 = top level, then 1, 2, ... for levels L-1, L-2, ...
 template <class Parents>
-static void run_stage(const Parents& par, const TvWs& w, const float4* tsph, PairOut out, RunOut runs,
-                      crsh_counters* ctr, int level_idx, unsigned B_paper, const DeviceInfo& dev, cudaStream_t s) {
-    const unsigned warps_grid = dev.sms * 8;   // 256-thread blocks
+static void run_stage(const Parents& par, const TvWs& w, unsigned stage, const float4* tsph, PairOut out,
+                      RunOut runs, crsh_counters* ctr, int level_idx, unsigned B_paper, const DeviceInfo& dev,
+                      cudaStream_t s) {
+    StageBuf sb = w.sb;
+    sb.work = w.work + 2 * stage;
     const unsigned sg = std::min<unsigned>(SC_GRID_MAX, dev.sms * 8);
-    k_unit_scan<Parents><<<1, 1024, 0, s>>>(par, w.sb, ctr, level_idx, B_paper);
-    k_count<Parents><<<warps_grid, 256, 0, s>>>(par, w.sb, tsph);
-    k_reduce<<<sg, SC_BLOCK, 0, s>>>(w.sb);
-    k_wordscan<<<sg, SC_BLOCK, 0, s>>>(w.sb, out, ctr, level_idx);
-    k_emit<Parents><<<warps_grid, 256, 0, s>>>(par, w.sb, out, runs);
+    // persistent grids: the count and emit passes claim unit batches
+    const unsigned gc = dev.sms * resident_blocks(k_count<Parents>, 256, dev);
+    const unsigned ge = dev.sms * resident_blocks(k_emit<Parents>, 256, dev);
+    k_unit_scan<Parents><<<1, 1024, 0, s>>>(par, sb, ctr, level_idx, B_paper);
+    k_count<Parents><<<gc, 256, 0, s>>>(par, sb, tsph);
+    k_reduce<<<sg, SC_BLOCK, 0, s>>>(sb);
+    k_wordscan<<<sg, SC_BLOCK, 0, s>>>(sb, out, ctr, level_idx);
+    k_emit<Parents><<<ge, 256, 0, s>>>(par, sb, out, runs);
 }
 
 crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const crsh_traverse_params* tp,
@@ -748,7 +860,7 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     k_compact<MeshOp><<<dev.sms * 2, TV_BLOCK, 0, s>>>(mop, TvCtl{w.st_mesh, &w.tile_ctr[0], ctr, -1});
     // top level: triangles of the accepted meshes
     TopParents top{w.mpN, w.mpM, &w.counts[0], sc->mesh_first_tri, level_nodes(L)};
-    run_stage(top, w, tsph, pairs_of(L), w.runs[L - 1], ctr, (int)L - 1, 0u, dev, s);
+    run_stage(top, w, 0u, tsph, pairs_of(L), w.runs[L - 1], ctr, (int)L - 1, 0u, dev, s);
     {
         const PairOut tp_out = pairs_of(L);
         k_runs_from_pairs<<<dev.sms * 4, 256, 0, s>>>(tp_out.node, tp_out.count, w.runs[L - 1]);
@@ -757,7 +869,7 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     for (unsigned l = L - 1; l >= 1; --l) {
         PairOut par = pairs_of(l + 1);
         LevelParents lp{par.tri, w.runs[l].start, w.runs[l].end, h->count + l, h->count + (l - 1), level_nodes(l), logB};
-        run_stage(lp, w, tsph, pairs_of(l), w.runs[l - 1], ctr, (int)l - 1, B, dev, s);
+        run_stage(lp, w, L - l, tsph, pairs_of(l), w.runs[l - 1], ctr, (int)l - 1, B, dev, s);
         if (l == 1) break;
     }
     {

@@ -160,6 +160,30 @@ def test_eq9_never_rejects_an_intersecting_sphere():
     assert rejected > 500 and accepted > 500
 
 
+def test_eq9_is_monotone_under_sphere_containment():
+    """Eq. 9 accepts iff the sphere meets the region |s| tan(a) + d sec(a) >= distance to the
+    axis, so a sphere that contains another is accepted whenever the inner one is (the GPU
+    traversal tests a chunk's bounding sphere first and skips children that reject it)."""
+    rng = np.random.default_rng(11)
+    tested = 0
+    for _ in range(20000):
+        C = rng.uniform(-2, 2, 3)
+        x = unit(rng.normal(size=3))
+        alpha = rng.uniform(0, 1.5)
+        d = rng.uniform(0, 0.3)
+        node = np.concatenate([C, [d], x, [alpha]])
+        K = rng.uniform(-6, 6, 3)
+        R = rng.uniform(0.01, 1.5)
+        # inner sphere, often touching the outer one from inside
+        r = R * rng.uniform(0, 1)
+        off = (R - r) * (1.0 if rng.uniform() < 0.5 else rng.uniform())
+        P = K + off * unit(rng.normal(size=3))
+        if oracle.sphere_cone(node, P, r):
+            tested += 1
+            assert oracle.sphere_cone(node, K, R), (node, K, R, P, r)
+    assert tested > 2000
+
+
 def test_eq9_closed_cases():
     node = np.array([0, 0, 0, 0.1, 0, 0, 1, 0.2])
     assert oracle.sphere_cone(node, (0, 0, 10), 0.0)                      # on the axis
