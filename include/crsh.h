@@ -138,8 +138,11 @@ typedef struct {
     const float *mesh_sphere;        /* 4 floats per mesh: centre xyz, radius (encloses the mesh) */
     uint32_t n_meshes;
     float *tri_sphere;               /* 4 floats per triangle, written by crsh_prepare_scene */
-    float *tri_mt;                   /* 12 floats per triangle, written by crsh_prepare_scene:
-                                        (v0, n.x), (v1 - v0, n.y), (v2 - v0, n.z), n = normal */
+    float *tri_mt;                   /* 16 floats per triangle (16-byte aligned), written by
+                                        crsh_prepare_scene: (v0, n.x), (v1 - v0, n.y),
+                                        (v2 - v0, n.z), (c, q): n = normal, c = centre of the
+                                        bounding sphere, q = squared radius of the pre-test of
+                                        the final tests */
 } crsh_scene;
 
 typedef struct {
@@ -183,8 +186,9 @@ const char *crsh_status_string(crsh_status s);
 
 /* Triangle bounding spheres (centroid centre, largest vertex distance, padded
  * outward for FP32 rounding) and the per-triangle record of the final tests
- * (v0, edges v1 - v0 and v2 - v0, normal).  Writes scene->tri_sphere and
- * scene->tri_mt. */
+ * (v0, edges v1 - v0 and v2 - v0, normal, and the bounding sphere the final
+ * tests check a ray's line against before Moller-Trumbore).  Writes
+ * scene->tri_sphere and scene->tri_mt. */
 crsh_status crsh_prepare_scene(const crsh_scene *scene, void *stream);
 
 /* Workspace bytes crsh_hash_sort needs for up to `capacity` rays generated

@@ -290,7 +290,8 @@ crsh_status build_launch(const crsh_rays* rays, const uint32_t* n_rays, const cr
 // ---------------------------------------------------------------------------
 // Scene preparation: triangle spheres (centroid, largest vertex distance,
 // padded outward by a few FP32 ulps of the coordinates) and the record read
-// by the final tests: v0, e1 = v1 - v0, e2 = v2 - v0 and n = e1 x e2.
+// by the final tests: v0, e1 = v1 - v0, e2 = v2 - v0, n = e1 x e2, and the
+// sphere with the pre-test's squared radius.
 // ---------------------------------------------------------------------------
 __global__ void k_prepare(crsh_scene sc) {
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < sc.n_tris; t += gridDim.x * blockDim.x) {
@@ -304,10 +305,13 @@ __global__ void k_prepare(crsh_scene sc) {
         reinterpret_cast<float4*>(sc.tri_sphere)[t] = make_float4(m.x, m.y, m.z, r);
         f3 e1 = b - a, e2 = c - a;
         f3 n = cross(e1, e2);
-        float4* mt = reinterpret_cast<float4*>(sc.tri_mt) + 3 * (size_t)t;
+        float4* mt = reinterpret_cast<float4*>(sc.tri_mt) + 4 * (size_t)t;
         mt[0] = make_float4(a.x, a.y, a.z, n.x);
         mt[1] = make_float4(e1.x, e1.y, e1.z, n.y);
         mt[2] = make_float4(e2.x, e2.y, e2.z, n.z);
+        // pre-test radius of the final tests, squared: 1.1 r^2 (with the
+        // grazing slack of the test, (a + b)^2 <= 1.1 a^2 + 11 b^2)
+        mt[3] = make_float4(m.x, m.y, m.z, 1.1f * r * r);
     }
 }
 

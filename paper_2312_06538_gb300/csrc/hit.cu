@@ -56,6 +56,27 @@ __device__ __forceinline__ bool mt_hit(float ox, float oy, float oz, float dx, f
 __device__ __forceinline__ unsigned long long hit_key(float t, unsigned tri) {
     return ((unsigned long long)__float_as_uint(t) << 32) | tri;
 }
+
+// Pre-test of a final test: a ray can only hit a triangle if its line passes
+// through the triangle's bounding sphere.  With v = c - o, s = v.d and
+// w = v - (s / |d|^2) d (the perpendicular from the line to the centre),
+// accept iff |w|^2 <= q + K s^2 / |d|^2, where q = 1.1 r^2 and K = 1.1e-7:
+// by (a + b)^2 <= 1.1 a^2 + 11 b^2 this holds whenever the distance is at
+// most r + 1e-4 x the distance along the ray, a slack far above the FP32
+// rounding of this test and of Moller-Trumbore's hit point even at grazing
+// incidence, so every triangle Moller-Trumbore would hit passes.  The brute
+// force takes the same pre-test, so both paths decide hits with one function.
+// id2 = 1 / |d|^2; a zero or non-finite direction rejects (as the test would).
+constexpr float PRETEST_K = 1.1e-7f;
+__device__ __forceinline__ bool near_line(float ox, float oy, float oz, float dx, float dy, float dz, float id2,
+                                          float4 C) {
+    const float vx = C.x - ox, vy = C.y - oy, vz = C.z - oz;
+    const float s = vx * dx + vy * dy + vz * dz;
+    const float tc = s * id2;
+    const float wx = vx - tc * dx, wy = vy - tc * dy, wz = vz - tc * dz;
+    const float w2 = wx * wx + wy * wy + wz * wz;
+    return w2 <= fmaf(s * PRETEST_K, tc, C.w);
+}
 constexpr unsigned long long NO_HIT = ~0ull;
 
 struct RaysDev {
@@ -79,11 +100,13 @@ __device__ __forceinline__ void flush_best(unsigned long long bk, bool rvalid, i
 }
 
 struct Ray7 {
-    float ox, oy, oz, dx, dy, dz, tmax;
+    float ox, oy, oz, dx, dy, dz, tmax, id2;
 };
 
 __device__ __forceinline__ Ray7 load_ray(const RaysDev& rays, unsigned i) {
-    return Ray7{rays.ox[i], rays.oy[i], rays.oz[i], rays.dx[i], rays.dy[i], rays.dz[i], rays.tmax[i]};
+    Ray7 r{rays.ox[i], rays.oy[i], rays.oz[i], rays.dx[i], rays.dy[i], rays.dz[i], rays.tmax[i], 0.f};
+    r.id2 = 1.0f / (r.dx * r.dx + r.dy * r.dy + r.dz * r.dz);
+    return r;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -115,7 +138,7 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
                                                       unsigned long long* best, unsigned* work, crsh_counters* ctr) {
     constexpr int H = B / 2;            // lanes per node (two rays each)
     constexpr int S = 32 / H;           // streams
-    __shared__ __align__(16) float4 s_tri[CH_WARPS][2][32][3];
+    __shared__ __align__(16) float4 s_tri[CH_WARPS][2][32][4];
     __shared__ unsigned s_tid[CH_WARPS][2][32];
     const unsigned P = (unsigned)min((unsigned long long)*p_count, p_cap);
     const unsigned N = *n_ptr;
@@ -149,10 +172,11 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
         // records of a group's triangles into buffer b (one commit per call)
         auto stage = [&](int b, unsigned cnt, unsigned pt) {
             if ((unsigned)lane < cnt) {
-                const float4* m = tri_mt + 3 * (size_t)pt;
+                const float4* m = tri_mt + 4 * (size_t)pt;
                 cp_async16(&s_tri[warp][b][lane][0], m);
                 cp_async16(&s_tri[warp][b][lane][1], m + 1);
                 cp_async16(&s_tri[warp][b][lane][2], m + 2);
+                cp_async16(&s_tri[warp][b][lane][3], m + 3);
                 s_tid[warp][b][lane] = pt;
             }
             cp_async_commit();
@@ -167,7 +191,7 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
         if (has1) window(q1, e1, pw1, pt1);
         unsigned ray0 = cur * B + r, ray1 = ray0 + H;
         bool v0 = ray0 < N, v1 = ray1 < N;
-        Ray7 a{0, 0, 0, 0, 0, 0, 0}, b{0, 0, 0, 0, 0, 0, 0};
+        Ray7 a{0, 0, 0, 0, 0, 0, 0, 0}, b{0, 0, 0, 0, 0, 0, 0, 0};
         if (v0) a = load_ray(rays, ray0);
         if (v1) b = load_ray(rays, ray1);
         unsigned long long k0 = NO_HIT, k1 = NO_HIT;
@@ -198,19 +222,32 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
             const unsigned nrays = min((unsigned)B, N - cur * B);
             if (lane == 0) n_tests += (unsigned long long)cnt * nrays;
             if (v0) {
-                for (unsigned j = sidx; j < cnt; j += S) {
+                // pre-test every (ray, triangle) of the lane; bit k = triangle sidx + S k
+                unsigned m0 = 0, m1 = 0;
+                unsigned k = 0;
+                for (unsigned j = sidx; j < cnt; j += S, ++k) {
+                    const float4 C = s_tri[warp][buf][j][3];
+                    m0 |= (unsigned)near_line(a.ox, a.oy, a.oz, a.dx, a.dy, a.dz, a.id2, C) << k;
+                    m1 |= (unsigned)(v1 && near_line(b.ox, b.oy, b.oz, b.dx, b.dy, b.dz, b.id2, C)) << k;
+                }
+                // Moller-Trumbore on the survivors
+                unsigned m = m0 | m1;
+                while (m) {
+                    const unsigned kk = __ffs(m) - 1;
+                    m &= m - 1;
+                    const unsigned j = sidx + S * kk;
                     const float4 A = s_tri[warp][buf][j][0], E1 = s_tri[warp][buf][j][1],
                                  E2 = s_tri[warp][buf][j][2];
                     float t;
-                    if (mt_hit(a.ox, a.oy, a.oz, a.dx, a.dy, a.dz, a.tmax, A, E1, E2, t)) {
+                    if (((m0 >> kk) & 1u) && mt_hit(a.ox, a.oy, a.oz, a.dx, a.dy, a.dz, a.tmax, A, E1, E2, t)) {
                         ++n_hits;
-                        const unsigned long long k = hit_key(t, s_tid[warp][buf][j]);
-                        k0 = k < k0 ? k : k0;
+                        const unsigned long long key = hit_key(t, s_tid[warp][buf][j]);
+                        k0 = key < k0 ? key : k0;
                     }
-                    if (v1 && mt_hit(b.ox, b.oy, b.oz, b.dx, b.dy, b.dz, b.tmax, A, E1, E2, t)) {
+                    if (((m1 >> kk) & 1u) && mt_hit(b.ox, b.oy, b.oz, b.dx, b.dy, b.dz, b.tmax, A, E1, E2, t)) {
                         ++n_hits;
-                        const unsigned long long k = hit_key(t, s_tid[warp][buf][j]);
-                        k1 = k < k1 ? k : k1;
+                        const unsigned long long key = hit_key(t, s_tid[warp][buf][j]);
+                        k1 = key < k1 ? key : k1;
                     }
                 }
             }
@@ -297,7 +334,7 @@ __global__ void k_finalize(RaysDev rays, const unsigned* n_ptr, crsh_scene sc, c
 constexpr int BF_BLOCK = 256;
 __global__ void __launch_bounds__(BF_BLOCK) k_brute(RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
                                                     unsigned n_tris, unsigned long long* best) {
-    __shared__ float4 s_tri[BF_BLOCK][3];
+    __shared__ float4 s_tri[BF_BLOCK][4];
     const unsigned n = *n_ptr;
     for (unsigned base = blockIdx.x * BF_BLOCK; base < n; base += gridDim.x * BF_BLOCK) {
         const unsigned i = base + threadIdx.x;
@@ -308,20 +345,23 @@ __global__ void __launch_bounds__(BF_BLOCK) k_brute(RaysDev rays, const unsigned
             dx = rays.dx[i]; dy = rays.dy[i]; dz = rays.dz[i];
             tmax = rays.tmax[i];
         }
+        const float id2 = 1.0f / (dx * dx + dy * dy + dz * dz);
         unsigned long long bk = NO_HIT;
         for (unsigned t0 = 0; t0 < n_tris; t0 += BF_BLOCK) {
             __syncthreads();
             if (t0 + threadIdx.x < n_tris) {
-                const float4* m = tri_mt + 3 * (size_t)(t0 + threadIdx.x);
+                const float4* m = tri_mt + 4 * (size_t)(t0 + threadIdx.x);
                 s_tri[threadIdx.x][0] = m[0];
                 s_tri[threadIdx.x][1] = m[1];
                 s_tri[threadIdx.x][2] = m[2];
+                s_tri[threadIdx.x][3] = m[3];
             }
             __syncthreads();
             const unsigned cnt = min((unsigned)BF_BLOCK, n_tris - t0);
             for (unsigned j = 0; j < cnt; ++j) {
                 float t;
-                if (mt_hit(ox, oy, oz, dx, dy, dz, tmax, s_tri[j][0], s_tri[j][1], s_tri[j][2], t)) {
+                if (near_line(ox, oy, oz, dx, dy, dz, id2, s_tri[j][3]) &&
+                    mt_hit(ox, oy, oz, dx, dy, dz, tmax, s_tri[j][0], s_tri[j][1], s_tri[j][2], t)) {
                     const unsigned long long k = hit_key(t, t0 + j);
                     bk = k < bk ? k : bk;
                 }

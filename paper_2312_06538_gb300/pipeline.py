@@ -58,7 +58,7 @@ class Pipeline:
         self.mesh_sphere = torch.from_numpy(np.ascontiguousarray(scene.mesh_sphere, np.float32)).to(dev)
         self.n_tris, self.n_meshes = scene.n_tris, scene.n_meshes
         self.tri_sphere = torch.empty((self.n_tris, 4), dtype=f32, device=dev)
-        self.tri_mt = torch.empty((self.n_tris, 12), dtype=f32, device=dev)
+        self.tri_mt = torch.empty((self.n_tris, 16), dtype=f32, device=dev)
         self.scene = C.crsh_scene(*[_ptr(self.scene_t[k]) for k in ("v0x", "v0y", "v0z", "v1x", "v1y", "v1z",
                                                                    "v2x", "v2y", "v2z")],
                                   self.n_tris, _ptr(self.mesh_first), _ptr(self.mesh_sphere), self.n_meshes,
