@@ -191,6 +191,15 @@ const char *crsh_status_string(crsh_status s);
  * scene->tri_sphere and scene->tri_mt. */
 crsh_status crsh_prepare_scene(const crsh_scene *scene, void *stream);
 
+/* The FP32 threshold tables the hash's direction bins compare against
+ * (Section 3.3.2 reading): cos_out[k] = fl32(cos(k pi / 2^theta_bits)) for
+ * k < 2^theta_bits and tan_out[j] = fl32(tan(j (pi/4) / M)) for j < M =
+ * 2^phi_bits / 8, each from an FP64 evaluation.  Device pointers (the caller
+ * owns them); theta_bits in [1, 13], phi_bits in [3, 13].  Asynchronous on
+ * `stream`; crsh_hash_sort builds the same tables in its workspace. */
+crsh_status crsh_hash_tables(uint32_t theta_bits, uint32_t phi_bits, float *cos_out, float *tan_out,
+                             void *stream);
+
 /* Workspace bytes crsh_hash_sort needs for up to `capacity` rays generated
  * from at most `max_pixels` G-buffer pixels (0 for crsh_rays_in input). */
 size_t crsh_hash_sort_workspace(uint32_t capacity, uint32_t max_pixels);

@@ -66,6 +66,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_generate_rays.argtypes = [U32] + [P] * 11 + [U32, P, I] + [P] * 10
         L.oracle_hash.restype = I
         L.oracle_hash.argtypes = [I64] + [P] * 8 + [ctypes.POINTER(_HashParams), P]
+        L.oracle_tables.restype = None
+        L.oracle_tables.argtypes = [U32, U32, P, P]
         L.oracle_stable_sort.restype = None
         L.oracle_stable_sort.argtypes = [I64, P, P]
         L.oracle_chunk_count.restype = I64
@@ -144,6 +146,15 @@ def hash_keys(rays: Dict[str, np.ndarray], lo, hi, **bits) -> np.ndarray:
     if rc != 0:
         raise ValueError("hash bit layout does not fit 32 bits")
     return keys
+
+
+def hash_tables(theta_bits: int, phi_bits: int):
+    """The hash's FP32 threshold tables: cos(k pi / 2^tb), k < 2^tb, and tan(j (pi/4) / M),
+    j < M = 2^pb / 8 (bin readings of Section 3.3.2)."""
+    c = np.empty(1 << theta_bits, np.float32)
+    t = np.empty((1 << phi_bits) // 8, np.float32)
+    lib().oracle_tables(int(theta_bits), int(phi_bits), _p(c), _p(t))
+    return c, t
 
 
 def stable_sort(keys: np.ndarray) -> np.ndarray:

@@ -244,6 +244,17 @@ static float* make_tan_table(uint32_t M) {
     return t;
 }
 
+/* The two threshold tables of a (theta bits, phi bits) layout, as the hash
+ * above builds them: 2^theta_bits cosines and 2^phi_bits / 8 tangents. */
+void oracle_tables(uint32_t theta_bits, uint32_t phi_bits, float* cos_out, float* tan_out) {
+    float* c = make_cos_table(1u << theta_bits);
+    float* t = make_tan_table((1u << phi_bits) / 8);
+    memcpy(cos_out, c, sizeof(float) * (1u << theta_bits));
+    memcpy(tan_out, t, sizeof(float) * ((1u << phi_bits) / 8));
+    free(c);
+    free(t);
+}
+
 /* Returns 0, or -1 for a parameter set the key layout cannot hold. */
 int oracle_hash(int64_t n, const float* ox, const float* oy, const float* oz, const float* dx,
                 const float* dy, const float* dz, const uint8_t* type, const uint8_t* light,

@@ -80,6 +80,7 @@ SIGNATURES = [
     ("crsh_version", ctypes.c_int, []),
     ("crsh_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("crsh_prepare_scene", ctypes.c_int, [ctypes.POINTER(crsh_scene), P]),
+    ("crsh_hash_tables", ctypes.c_int, [U32, U32, P, P, P]),
     ("crsh_hash_sort_workspace", ctypes.c_size_t, [U32, U32]),
     ("crsh_hash_sort", ctypes.c_int,
      [ctypes.POINTER(crsh_gbuffer), ctypes.POINTER(crsh_rays_in), P, U32, ctypes.POINTER(crsh_hash_params),
@@ -148,6 +149,10 @@ def crsh_version() -> int:
 
 def crsh_prepare_scene(scene: crsh_scene, stream: int):
     _check("crsh_prepare_scene", load().crsh_prepare_scene(ctypes.byref(scene), P(stream)))
+
+
+def crsh_hash_tables(theta_bits: int, phi_bits: int, cos_out: int, tan_out: int, stream: int):
+    _check("crsh_hash_tables", load().crsh_hash_tables(theta_bits, phi_bits, P(cos_out), P(tan_out), P(stream)))
 
 
 def crsh_hash_sort_workspace(capacity: int, max_pixels: int) -> int:

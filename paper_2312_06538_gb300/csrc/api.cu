@@ -78,6 +78,17 @@ crsh_status crsh_prepare_scene(const crsh_scene* scene, void* stream) {
     return prepare_scene_launch(scene, static_cast<cudaStream_t>(stream), dev);
 }
 
+crsh_status crsh_hash_tables(uint32_t theta_bits, uint32_t phi_bits, float* cos_out, float* tan_out, void* stream) {
+    if (theta_bits < 1 || theta_bits > 13 || phi_bits < 3 || phi_bits > 13 || !cos_out || !tan_out)
+        return CRSH_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if (!current_device(dev)) return CRSH_ERR_CUDA;
+    tables_launch(TableSpec{{cos_out, tan_out, nullptr, nullptr}, {1u << theta_bits, (1u << phi_bits) / 8, 0, 0},
+                            {0, 1, 0, 0}},
+                  static_cast<cudaStream_t>(stream), dev);
+    return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
+}
+
 size_t crsh_hash_sort_workspace(uint32_t capacity, uint32_t max_pixels) {
     return hash_sort_workspace(capacity, max_pixels);
 }

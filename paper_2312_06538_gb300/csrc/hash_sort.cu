@@ -33,8 +33,8 @@ struct GenRay {
     uint8_t type, light;
 };
 
-// Tables: theta thresholds cos(k pi / 2^tb) and phi thresholds tan(j pi / 2^pb),
-// rounded to FP32, built on the host and copied in through kernel parameters.
+// Tables: theta thresholds cos(k pi / 2^tb) and phi thresholds
+// tan(j (pi/4) / M), M = 2^pb / 8, rounded to FP32 (k_tables).
 struct HashDev {
     const float* cosS;  // 2^stb entries
     const float* tanS;  // 2^spb / 8 entries
@@ -288,10 +288,26 @@ __global__ void k_gen_rays(crsh_rays_in in, HashDev h, GenOut out, unsigned* n_o
     }
 }
 
-// Loads host-built threshold tables through kernel parameters (capturable,
-// no pageable copies).
-__global__ void k_put_table(TableChunk c, float* dst) {
-    for (unsigned i = threadIdx.x; i < c.count; i += blockDim.x) dst[c.offset + i] = c.v[i];
+// Threshold tables of the bins: cos(k pi / B) for k < B and tan(j (pi/4) / M)
+// for j < M, each evaluated in FP64 from the same FP64 argument expression as
+// the definition and rounded to FP32; one thread per entry.
+__global__ void k_tables(TableSpec t) {
+    const double pi = 3.14159265358979323846;
+    unsigned total = 0;
+    for (int i = 0; i < 4; ++i) total += t.n[i];
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        unsigned i = 0, k = e;
+        while (k >= t.n[i]) k -= t.n[i++];
+        t.dst[i][k] = t.is_tan[i] ? (float)tan((double)k * (pi / 4.0) / (double)t.n[i])
+                                  : (float)cos((double)k * pi / (double)t.n[i]);
+    }
+}
+
+void tables_launch(const TableSpec& t, cudaStream_t s, const DeviceInfo& dev) {
+    const unsigned total = t.n[0] + t.n[1] + t.n[2] + t.n[3];
+    const unsigned blocks = (total + 255) / 256;
+    const unsigned grid = blocks < (unsigned)dev.sms ? (blocks ? blocks : 1) : dev.sms;
+    k_tables<<<grid, 256, 0, s>>>(t);
 }
 
 // ---------------------------------------------------------------------------
@@ -507,9 +523,27 @@ void radix_sort_launch(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, c
                                                 rw.status + (size_t)p * rs_tiles * 256, &rw.tile_ctr[p], ctr);
 }
 
+struct SortedOut {
+    float *ox, *oy, *oz, *dx, *dy, *dz, *tmax;
+    uint8_t* type;
+    uint32_t *ray_id, *pixel, *keys;
+};
+
+__device__ __forceinline__ void copy_ray(const GenOut& gen, unsigned src, const SortedOut& out, unsigned i,
+                                         unsigned key) {
+    out.ox[i] = gen.ox[src]; out.oy[i] = gen.oy[src]; out.oz[i] = gen.oz[src];
+    out.dx[i] = gen.dx[src]; out.dy[i] = gen.dy[src]; out.dz[i] = gen.dz[src];
+    out.tmax[i] = gen.tmax[src];
+    out.type[i] = gen.type[src];
+    out.pixel[i] = gen.pixel[src];
+    out.ray_id[i] = src;
+    out.keys[i] = key;
+}
+
 // ---------------------------------------------------------------------------
 // Section 3.3.5: decompression.  Chunk sizes in sorted order, exclusive scan
-// (the skeleton), then every sorted position finds its chunk.
+// (the skeleton: the sorted position of each chunk's first ray), then every
+// sorted position finds its chunk (k_gather).
 // ---------------------------------------------------------------------------
 constexpr int SCAN_BLOCK = 256, SCAN_ITEMS = 4, SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 
@@ -563,45 +597,55 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_pos(const uint32_t* kA, co
     }
 }
 
-struct SortedOut {
-    float *ox, *oy, *oz, *dx, *dy, *dz, *tmax;
-    uint8_t* type;
-    uint32_t *ray_id, *pixel, *keys;
-};
-
 // mode 0: generation order; 1: sorted (value = ray index); 2: sorted chunks.
+// Warps walk contiguous runs of 32-ray groups; in mode 2 the 32 rays of a
+// group lie in at most 32 consecutive chunks from the chunk of its first ray
+// (every chunk holds a ray), so lane l holds that window's start position l,
+// each ray finds its chunk by a binary search over the lanes, and the next
+// group starts from its first ray's chunk (the last ray's or the one after).
 __global__ void k_gather(int mode, GenOut gen, const uint32_t* kA, const uint32_t* vA, const uint32_t* kB,
                          const uint32_t* vB, const unsigned* plan, const uint32_t* cbase, const uint32_t* cpos,
                          const unsigned* c_ptr, const unsigned* n_ptr, SortedOut out) {
     const unsigned n = *n_ptr;
-    const unsigned C = (mode == 2) ? *c_ptr : 0;
     const uint32_t* sv = (mode != 0 && plan[4]) ? vB : vA;
     const uint32_t* sk = (mode != 0 && plan[4]) ? kB : kA;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        unsigned src, key;
-        if (mode == 0) {
-            src = i;
-            key = gen.key[i];
-        } else if (mode == 1) {
-            src = sv[i];
-            key = sk[i];
-        } else {
-            // last sorted chunk whose start is <= i
-            unsigned lo = 0, hi = C - 1;
-            while (lo < hi) {
-                unsigned mid = lo + (hi - lo + 1) / 2;
-                if (cpos[mid] <= i) lo = mid; else hi = mid - 1;
-            }
-            src = cbase[sv[lo]] + (i - cpos[lo]);
-            key = sk[lo];
+    if (mode != 2) {
+        for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const unsigned src = mode == 0 ? i : sv[i];
+            const unsigned key = mode == 0 ? gen.key[i] : sk[i];
+            copy_ray(gen, src, out, i, key);
         }
-        out.ox[i] = gen.ox[src]; out.oy[i] = gen.oy[src]; out.oz[i] = gen.oz[src];
-        out.dx[i] = gen.dx[src]; out.dy[i] = gen.dy[src]; out.dz[i] = gen.dz[src];
-        out.tmax[i] = gen.tmax[src];
-        out.type[i] = gen.type[src];
-        out.pixel[i] = gen.pixel[src];
-        out.ray_id[i] = src;
-        out.keys[i] = key;
+        return;
+    }
+    const unsigned C = *c_ptr;
+    const int lane = threadIdx.x & 31;
+    const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const unsigned groups = (n + 31) / 32, per = (groups + nw - 1) / nw;
+    const unsigned g0 = min(groups, gw * per), g1 = min(groups, g0 + per);
+    if (g0 >= g1 || C == 0) return;
+    unsigned lo = 0, hi = C - 1;   // last chunk starting at or before the first ray
+    while (lo < hi) {
+        const unsigned mid = lo + (hi - lo + 1) / 2;
+        if (cpos[mid] <= g0 * 32) lo = mid; else hi = mid - 1;
+    }
+    for (unsigned g = g0; g < g1; ++g) {
+        const unsigned i = g * 32 + lane;
+        const unsigned cl = (lo + lane < C) ? cpos[lo + lane] : 0xffffffffu;
+        unsigned l = 0;
+#pragma unroll
+        for (unsigned step = 16; step > 0; step >>= 1) {
+            const unsigned v = __shfl_sync(FULL, cl, l + step);
+            if (v <= i) l += step;
+        }
+        const unsigned start = __shfl_sync(FULL, cl, l);
+        const unsigned chunk = lo + l;
+        if (i < n) copy_ray(gen, cbase[sv[chunk]] + (i - start), out, i, sk[chunk]);
+        // chunk of the next group's first ray: the last ray's chunk or the one after it
+        const unsigned l31 = __shfl_sync(FULL, l, 31);
+        const unsigned after = __shfl_sync(FULL, cl, min(l31 + 1, 31u));
+        const unsigned nxt = l31 < 31 ? after : (lo + 32 < C ? cpos[lo + 32] : 0xffffffffu);
+        lo = lo + l31 + (nxt <= (g + 1) * 32 ? 1u : 0u);
+        lo = min(lo, C - 1);
     }
 }
 
@@ -686,16 +730,6 @@ size_t hash_sort_workspace(uint32_t cap, uint32_t max_pixels) {
     return carve_hash(nullptr, cap, max_pixels).total;
 }
 
-static void put_table(float* dst, const float* src, unsigned count, cudaStream_t s) {
-    for (unsigned off = 0; off < count; off += TableChunk::kMax) {
-        TableChunk c;
-        c.offset = off;
-        c.count = count - off < TableChunk::kMax ? count - off : TableChunk::kMax;
-        for (unsigned i = 0; i < c.count; ++i) c.v[i] = src[off + i];
-        k_put_table<<<1, 256, 0, s>>>(c, dst);
-    }
-}
-
 crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, const float* lights, uint32_t n_lights,
                              const crsh_hash_params* hp, crsh_rays* out, uint32_t* keys_out, uint32_t* n_out,
                              crsh_counters* ctr, void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev) {
@@ -711,16 +745,7 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
     float* ttanS = tcosS + BS;
     float* tcosR = ttanS + MS;
     float* ttanR = tcosR + BR;
-    {
-        static thread_local float host[(1u << 13) * 2 + (1u << 13) / 8 * 2];
-        const double pi = 3.14159265358979323846;
-        unsigned o = 0;
-        for (unsigned k = 0; k < BS; ++k) host[o++] = (float)cos((double)k * pi / (double)BS);
-        for (unsigned j = 0; j < MS; ++j) host[o++] = (float)tan((double)j * (pi / 4.0) / (double)MS);
-        for (unsigned k = 0; k < BR; ++k) host[o++] = (float)cos((double)k * pi / (double)BR);
-        for (unsigned j = 0; j < MR; ++j) host[o++] = (float)tan((double)j * (pi / 4.0) / (double)MR);
-        put_table(w.tables, host, o, s);
-    }
+    tables_launch(TableSpec{{tcosS, ttanS, tcosR, ttanR}, {BS, MS, BR, MR}, {0, 1, 0, 1}}, s, dev);
     HashDev h;
     h.cosS = tcosS; h.tanS = ttanS; h.cosR = tcosR; h.tanR = ttanR;
     for (int a = 0; a < 3; ++a) { h.lo[a] = hp->lo[a]; h.hi[a] = hp->hi[a]; }
@@ -773,7 +798,7 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
                  out->ray_id, out->pixel, keys_out};
     {
         unsigned blocks = (cap + 255) / 256;
-        if (blocks > (unsigned)persist) blocks = persist;
+        if (blocks > (unsigned)dev.sms * 4) blocks = dev.sms * 4;
         if (blocks == 0) blocks = 1;
         const int mode = !sort ? 0 : (compress ? 2 : 1);
         k_gather<<<blocks, 256, 0, s>>>(mode, w.gen, kA, vA, w.altK, w.altV, w.plan, w.chBase, w.chPos, cnt_ptr,

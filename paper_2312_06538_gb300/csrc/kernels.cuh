@@ -15,12 +15,14 @@ struct DeviceInfo {
     int sms = 0;
 };
 
-// A slice of a host-built FP32 table passed to a kernel by value.
-struct TableChunk {
-    static constexpr unsigned kMax = 4096;
-    unsigned offset, count;
-    float v[kMax];
+// Up to four bin threshold tables to fill (hash_sort.cu): entry k of table i
+// is cos(k pi / n[i]) or, when is_tan[i], tan(k (pi/4) / n[i]), in FP32.
+struct TableSpec {
+    float* dst[4];
+    unsigned n[4];
+    int is_tan[4];
 };
+void tables_launch(const TableSpec& t, cudaStream_t s, const DeviceInfo& dev);
 
 // One-sweep LSD radix sort of 32-bit (key, value) pairs (hash_sort.cu).
 struct RadixWs {

@@ -408,25 +408,29 @@ struct UnitStream {
     }
 };
 
+__device__ __forceinline__ float warp_min_f(float v) {
+    float r;
+    asm("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+    float r;
+    asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 // Bounding sphere of the chunk's triangle spheres (warp-uniform): centre the
-// mean of the valid lanes' centres, radius the largest |c_i - K| + r_i, padded
-// outward like a triangle sphere (FP32 rounding of this radius and of the
-// eq. 9 evaluation), so the exact sphere contains every triangle sphere.
+// middle of the centres' bounding box, radius the largest |c_i - K| + r_i,
+// padded outward like a triangle sphere (FP32 rounding of this radius and of
+// the eq. 9 evaluation), so the exact sphere contains every triangle sphere.
 __device__ __forceinline__ float4 chunk_sphere(float4 ts, bool valid) {
-    const unsigned nv = __popc(__ballot_sync(FULL, valid));
-    float sx = valid ? ts.x : 0.f, sy = valid ? ts.y : 0.f, sz = valid ? ts.z : 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(FULL, sx, o);
-        sy += __shfl_xor_sync(FULL, sy, o);
-        sz += __shfl_xor_sync(FULL, sz, o);
-    }
-    const float inv = 1.0f / (float)nv;
-    const float kx = sx * inv, ky = sy * inv, kz = sz * inv;
+    const float inf = __int_as_float(0x7f800000);
+    const float lx = warp_min_f(valid ? ts.x : inf), hx = warp_max_f(valid ? ts.x : -inf);
+    const float ly = warp_min_f(valid ? ts.y : inf), hy = warp_max_f(valid ? ts.y : -inf);
+    const float lz = warp_min_f(valid ? ts.z : inf), hz = warp_max_f(valid ? ts.z : -inf);
+    const float kx = 0.5f * (lx + hx), ky = 0.5f * (ly + hy), kz = 0.5f * (lz + hz);
     const float dx = ts.x - kx, dy = ts.y - ky, dz = ts.z - kz;
-    float R = valid ? sqrtf(dx * dx + dy * dy + dz * dz) + ts.w : 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(FULL, R, o));
+    float R = warp_max_f(valid ? sqrtf(dx * dx + dy * dy + dz * dz) + ts.w : 0.f);
     const float mag = fabsf(kx) + fabsf(ky) + fabsf(kz) + R;
     R = R * (1.0f + 9.6e-7f) + 3.9e-6f * mag;
     return make_float4(kx, ky, kz, R);

@@ -46,6 +46,30 @@ def case(request):
     return w, p, c, ref
 
 
+def test_hash_tables_bit_exact_for_every_layout():
+    """The device-built bin tables equal the oracle's (FP64 libm on the host, rounded to
+    FP32) for every theta width 1..13 and phi width 3..13 the hash accepts."""
+    import torch
+    from paper_2312_06538_gb300 import crsh as C
+    s = torch.cuda.current_stream().cuda_stream
+    for tb in range(1, 14):
+        pb = max(3, tb)
+        c = torch.empty(1 << tb, dtype=torch.float32, device="cuda")
+        t = torch.empty(max(1, (1 << pb) // 8), dtype=torch.float32, device="cuda")
+        C.crsh_hash_tables(tb, pb, c.data_ptr(), t.data_ptr(), s)
+        rc, rt = oracle.hash_tables(tb, pb)
+        torch.cuda.synchronize()
+        assert np.array_equal(c.cpu().numpy().view(np.uint32), rc.view(np.uint32)), tb
+        assert np.array_equal(t.cpu().numpy().view(np.uint32), rt.view(np.uint32)), pb
+    for pb in range(3, 14):   # every phi width with a small theta table
+        c = torch.empty(2, dtype=torch.float32, device="cuda")
+        t = torch.empty((1 << pb) // 8, dtype=torch.float32, device="cuda")
+        C.crsh_hash_tables(1, pb, c.data_ptr(), t.data_ptr(), s)
+        _, rt = oracle.hash_tables(1, pb)
+        torch.cuda.synchronize()
+        assert np.array_equal(t.cpu().numpy().view(np.uint32), rt.view(np.uint32)), pb
+
+
 def test_rays_keys_and_order_bit_exact(case):
     w, p, c, ref = case
     got = p.sorted_rays()
