@@ -217,7 +217,7 @@ def closest_traffic():
 
 def launches_per_step(levels: int, compress: bool) -> int:
     """Kernels of libcrsh.so launched by one pass (count of <<<>>> in the call sequence)."""
-    hash_sort = 3 + 1 + (1 if compress else 0) + 2 + 4 + (1 if compress else 0) + 1   # tables, gen, chunk, hist+plan, 4 passes, pos, gather
+    hash_sort = 1 + 1 + (1 if compress else 0) + 2 + 4 + (1 if compress else 0) + 1   # tables, gen, chunk, hist+plan, 4 passes, pos, gather
     build = levels
     traverse = 1 + 5 + 1 + 5 * (levels - 1) + 1   # mesh stage, top stage + its runs, 5 kernels per level, csr
     closest = 3
@@ -353,6 +353,114 @@ def batched_comparison(dev, n_batches=32, reps=5):
     return out
 
 
+def fp32_probe(dev, stream, reps: int = 5):
+    """Measured FP32 FMA throughput (crsh_fma_probe: 8 independent FMA chains per thread,
+    full occupancy), best of reps, CUDA events on the stream."""
+    import torch
+    from paper_2312_06538_gb300 import crsh as C
+    props = torch.cuda.get_device_properties(dev)
+    blocks = props.multi_processor_count * 8
+    out = torch.empty(blocks, dtype=torch.float32, device=dev)
+    sh = stream.cuda_stream
+    C.crsh_fma_probe(out.data_ptr(), 1000, blocks, sh)       # warm-up
+    best = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        flops = C.crsh_fma_probe(out.data_ptr(), 50000, blocks, sh)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        best = max(best, flops / (a.elapsed_time(b) * 1e-3) / 1e12)
+    return best
+
+
+def tiled_gbuffer(w, tiles: int, seed: int = 77):
+    """`tiles` copies of the frame's G-buffer, each shifted (up to 0.05 per axis) and with
+    normals and incident directions turned by a small seeded rotation (up to 0.02 rad), so
+    keys stay spread like a larger frame's."""
+    rng = np.random.default_rng(seed)
+    parts = {k: [] for k in w.gbuffer}
+    for t in range(tiles):
+        shift = rng.uniform(-0.05, 0.05, 3).astype(np.float32) if t else np.zeros(3, np.float32)
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        ang = rng.uniform(0, 0.02) if t else 0.0
+        K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        R = (np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K).astype(np.float32)
+        g = w.gbuffer
+        P = np.stack([g["px"], g["py"], g["pz"]], 1) + shift
+        Nn = np.stack([g["nx"], g["ny"], g["nz"]], 1) @ R.T
+        I = np.stack([g["ix"], g["iy"], g["iz"]], 1) @ R.T
+        Nn /= np.linalg.norm(Nn, axis=1, keepdims=True).clip(1e-30)
+        I /= np.linalg.norm(I, axis=1, keepdims=True).clip(1e-30)
+        for k, col in (("px", P[:, 0]), ("py", P[:, 1]), ("pz", P[:, 2]), ("nx", Nn[:, 0]), ("ny", Nn[:, 1]),
+                       ("nz", Nn[:, 2]), ("ix", I[:, 0]), ("iy", I[:, 1]), ("iz", I[:, 2])):
+            parts[k].append(np.ascontiguousarray(col, np.float32))
+        parts["material"].append(g["material"])
+        parts["hit"].append(g["hit"])
+    return {k: np.concatenate(v) for k, v in parts.items()}
+
+
+def hbm_sweep(args, tiles_list=(1, 2, 4, 8, 16, 22), reps: int = 20):
+    """Hash+sort (one crsh_hash_sort call: generation, hashing, trimming, compression, 4-pass
+    radix sort, decompression + gather) and build (crsh_build) at 3M..70M rays: G-buffers of
+    1..22 perturbed tiles of the 1024x1024 frame of config 3.  Algorithmic bytes per call:
+    hash 41 B per pixel read + 41 B per ray written, sort 16 B per sorted chunk (one read and
+    one write of key and value), decompress + gather 4 + 33 + 41 B per ray; build 28 B per ray
+    read + 40 B per level-1 node written.  Median of reps, L2 flushed before each."""
+    import synthetic
+    import torch
+    from paper_2312_06538_gb300 import pipeline as pl
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    w = synthetic.make(3)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    lights = torch.from_numpy(w.lights).to(dev)
+    for tiles in tiles_list:
+        g = tiled_gbuffer(w, tiles)
+        npx = g["hit"].shape[0]
+        p = pl.Pipeline(w.scene, max_pixels=npx, n_lights=w.lights.shape[0], bundle=w.bundle, levels=w.levels,
+                        ray_capacity=npx * 4, pair_capacity=1 << 16, device=dev)
+        hp, bp = pl.workload_params(w)
+        gd = p.gbuffer_to_device(g, dev)
+        gs = p.gbuffer_struct(gd)
+        p.hash_sort(gs, lights, hp, sh)
+        p.build(bp, sh)
+        c = p.read_counters()
+        n, chunks = c["rays"], c["chunks"]
+
+        def med(fn):
+            ts = []
+            warm = 3 if reps >= 3 else 1
+            for k in range(reps + warm):
+                flush.fill_(k & 0xff)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                if k >= warm:
+                    ts.append(a.elapsed_time(b))
+            return statistics.median(ts)
+        t_hash = med(lambda: p.hash_sort(gs, lights, hp, sh))
+        t_build = med(lambda: p.build(bp, sh))
+        b_hash = 41 * npx + 41 * n + 16 * chunks + (4 + 33 + 41) * n
+        b_build = 28 * n + 40 * ((n + w.bundle - 1) // w.bundle)
+        line = {"sweep": "hash_sort+build HBM", "pixels": npx, "rays": n, "chunks": chunks,
+                "hash_sort_ms": t_hash, "hash_sort_gbs": b_hash / (t_hash * 1e-3) / 1e9,
+                "hash_sort_frac": b_hash / (t_hash * 1e-3) / 1e9 / hbm,
+                "build_ms": t_build, "build_gbs": b_build / (t_build * 1e-3) / 1e9,
+                "build_frac": b_build / (t_build * 1e-3) / 1e9 / hbm,
+                "peak_gbs": hbm, "peak_source": src,
+                "mrays_per_s_hash_sort_build": n / ((t_hash + t_build) * 1e-3) / 1e6}
+        print(json.dumps(line), flush=True)
+        del p, gd, gs
+        torch.cuda.empty_cache()
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -448,7 +556,8 @@ def run_gpu(args, w):
     peaks, peak_src = _peaks()
     clocks = clk.summary()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tf = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    peak_derived = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    peak_tf = fp32_probe(dev, stream)
     ch_ms = float(stage[:, 3].mean())
     achieved = c["final_tests"] * MT_FLOPS / (ch_ms * 1e-3) / 1e12
     tr_ms = float(stage[:, 2].mean())
@@ -457,9 +566,12 @@ def run_gpu(args, w):
     roofline = {"kernel": "crsh_closest_hit (k_closest + fill + finalize)", "bound": "alu",
                 "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
                 "traffic": traffic,
-                "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                               f"(max SM clock, {peak_src} peaks file)",
-                "algorithmic": f"{MT_FLOPS} FP32 flops per ray-triangle test x {c['final_tests']} tests per launch"}
+                "peak_source": "measured: crsh_fma_probe (FP32 FMA chains at full occupancy, best of 5, burst)",
+                "peak_derived": peak_derived,
+                "peak_derived_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                       f"(max SM clock, {peak_src} peaks file)",
+                "algorithmic": f"{MT_FLOPS} FP32 flops (one Moller-Trumbore test) per candidate ray-triangle test x "
+                               f"{c['final_tests']} candidate tests per launch"}
     total_tests = c["final_tests"] + eq9_tests
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -518,8 +630,18 @@ def main():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="hash/sort/build HBM sweep at 3M..70M rays (one JSON line per size) instead of the step")
+    ap.add_argument("--sweep-tiles", type=int, nargs="*", default=None, help="sweep sizes in frame tiles")
+    ap.add_argument("--sweep-reps", type=int, default=20)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
+    if args.sweep:
+        if args.sweep_tiles:
+            hbm_sweep(args, tiles_list=tuple(args.sweep_tiles), reps=args.sweep_reps)
+        else:
+            hbm_sweep(args, reps=args.sweep_reps)
+        return
     import synthetic
     w = synthetic.make(args.config, res=args.res)
     if args.impl == "reference":

@@ -81,6 +81,7 @@ SIGNATURES = [
     ("crsh_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("crsh_prepare_scene", ctypes.c_int, [ctypes.POINTER(crsh_scene), P]),
     ("crsh_hash_tables", ctypes.c_int, [U32, U32, P, P, P]),
+    ("crsh_fma_probe", ctypes.c_int, [P, U32, U32, ctypes.POINTER(ctypes.c_ulonglong), P]),
     ("crsh_hash_sort_workspace", ctypes.c_size_t, [U32, U32]),
     ("crsh_hash_sort", ctypes.c_int,
      [ctypes.POINTER(crsh_gbuffer), ctypes.POINTER(crsh_rays_in), P, U32, ctypes.POINTER(crsh_hash_params),
@@ -149,6 +150,13 @@ def crsh_version() -> int:
 
 def crsh_prepare_scene(scene: crsh_scene, stream: int):
     _check("crsh_prepare_scene", load().crsh_prepare_scene(ctypes.byref(scene), P(stream)))
+
+
+def crsh_fma_probe(out: int, iters: int, blocks: int, stream: int) -> int:
+    """Launches the FP32 FMA probe; returns the flops it performs."""
+    f = ctypes.c_ulonglong(0)
+    _check("crsh_fma_probe", load().crsh_fma_probe(P(out), iters, blocks, ctypes.byref(f), P(stream)))
+    return int(f.value)
 
 
 def crsh_hash_tables(theta_bits: int, phi_bits: int, cos_out: int, tan_out: int, stream: int):

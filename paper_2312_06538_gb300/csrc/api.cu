@@ -78,6 +78,12 @@ crsh_status crsh_prepare_scene(const crsh_scene* scene, void* stream) {
     return prepare_scene_launch(scene, static_cast<cudaStream_t>(stream), dev);
 }
 
+crsh_status crsh_fma_probe(float* out, uint32_t iters, uint32_t blocks, unsigned long long* flops, void* stream) {
+    if (!out || !flops || iters < 1 || blocks < 1 || blocks > (1u << 20)) return CRSH_ERR_INVALID_ARG;
+    *flops = fma_probe_launch(out, iters, blocks, static_cast<cudaStream_t>(stream));
+    return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
+}
+
 crsh_status crsh_hash_tables(uint32_t theta_bits, uint32_t phi_bits, float* cos_out, float* tan_out, void* stream) {
     if (theta_bits < 1 || theta_bits > 13 || phi_bits < 3 || phi_bits > 13 || !cos_out || !tan_out)
         return CRSH_ERR_INVALID_ARG;

@@ -2,11 +2,10 @@
 // data the traversal and final tests read (triangle bounding spheres,
 // Moller-Trumbore edge layout).
 //
-// GB300 design: a warp builds 32 level-1 nodes.  Rays are read coalesced,
-// the spheres (eqs. 7-8) merge as balanced binary trees of shuffle-downs
-// within B-lane groups, and the directions pass through shared memory so
-// that lane k folds node k's cone ray by ray (eqs. 1-4).  Upper levels merge
-// their B children in B-lane groups (eqs. 5-8).  Every node is padded outward after its merge so the FP32
+// GB300 design: a warp builds 32 level-1 nodes.  Rays are staged in shared
+// memory with all loads in flight, then lane k builds node k: the sphere tree
+// (eqs. 7-8) in place and the cone fold (eqs. 1-4).  Upper levels merge their
+// B children in B-lane groups, as balanced trees of shuffle-downs (eqs. 5-8).  Every node is padded outward after its merge so the FP32
 // hierarchy contains its rays, and stores tan(spread), 1/cos(spread) for the
 // eq. 9 tests of the traversal.
 #include "common.cuh"
@@ -43,33 +42,55 @@ __device__ __forceinline__ void cone_union(SC& a, const SC& b) {
     a.phi = fminf(PI_F, 0.5f * th + fmaxf(a.phi, b.phi));
 }
 
-// eqs. 1-4: widen (x, phi) to hold direction r: far edge e of the current cone
-// (eq. 2, with q the unit normal to x in the plane of x and r pointing away
-// from r, eq. 1), new axis the bisector of e and r (eq. 3), new spread the
-// angle between axis and r (eq. 4).  When the result would be a cone of
-// half-angle >= pi/2 (theta + phi >= pi), the node takes the whole sphere,
-// which eq. 9 accepts everywhere anyway.
-__device__ __forceinline__ void cone_add_ray(f3& x, float& phi, f3 r) {
-    if (phi >= PI_F) return;
-    float th = angle(x, r);
-    if (th <= phi) return;
-    if (th + phi >= PI_F - 1e-6f) {
-        phi = PI_F;
-        return;
+// eqs. 1-4: widen the cone (x, phi) to hold direction r.  When r lies outside
+// (theta = angle(x, r) > phi), the far edge e of the cone in the plane of x
+// and r (eqs. 1-2) and r span the new cone: axis the bisector of e and r
+// (eq. 3), spread the angle from the axis to r (eq. 4).  In closed form the
+// new spread is (phi + theta) / 2 and the axis turns toward r by
+// (theta - phi) / 2; the fold is carried as (axis, cos phi, sin phi), and the
+// sine and cosine of every angle a step needs follow from products of these
+// and of cos theta = x.r, sin theta = |x x r|, with tangent half-angle
+// formulas for the halved angles.  Only multiplies, adds, a few reciprocals
+// and square roots, and stable at small angles (sines are never taken from
+// cosines).  A result whose half-angle would reach pi/2 (theta + phi >=
+// pi - 1e-6) is the whole sphere, which eq. 9 accepts everywhere anyway.
+struct ConeFold {
+    f3 x;
+    float cp, sp;   // cos, sin of the spread
+    bool full;
+    __device__ __forceinline__ void start(f3 d) {
+        x = d;
+        cp = 1.0f;
+        sp = 0.0f;
+        full = false;
     }
-    f3 q = cross(cross(r, x), x);
-    float lq = len(q);
-    if (!(lq > 0.0f)) {   // r numerically parallel to x: nothing to widen
-        phi = fmaxf(phi, th);
-        return;
+    __device__ __forceinline__ void add(f3 r) {
+        if (full) return;
+        const float c = dot(x, r);
+        const f3 w = cross(x, r);
+        const float s = sqrtf(dot(w, w));
+        // inside iff theta <= phi: sin(phi - theta) >= 0, excluding phi - theta = -pi
+        const float sd = sp * c - cp * s, cd = cp * c + sp * s;   // sin, cos of (phi - theta)
+        if (sd > 0.0f || (sd == 0.0f && cd > 0.0f)) return;
+        const float ss = sp * c + cp * s, cs = cp * c - sp * s;   // sin, cos of (phi + theta)
+        if (ss < 0.0f || (ss <= 1e-6f && cs < 0.0f)) {            // theta + phi >= pi - 1e-6
+            full = true;
+            return;
+        }
+        // turn the axis toward r by delta = (theta - phi) / 2: tan(delta) = sin(2 delta) / (1 + cos(2 delta))
+        // = (1 - cos(2 delta)) / sin(2 delta), whichever side has no cancellation
+        const float td = cd >= 0.0f ? -sd / (1.0f + cd) : (1.0f - cd) / -sd;
+        const float cdl = rsqrtf(1.0f + td * td), sdl = td * cdl;
+        const float is = 1.0f / s;
+        const f3 u = (r - x * c) * is;                              // unit normal to x toward r
+        x = unit(x * cdl + u * sdl);
+        // new spread (phi + theta) / 2: tan = sin(phi + theta) / (1 + cos(phi + theta)), or its other form
+        const float tp = cs >= 0.0f ? ss / (1.0f + cs) : (1.0f - cs) / ss;
+        cp = rsqrtf(1.0f + tp * tp);
+        sp = tp * cp;
     }
-    q = q * (1.0f / lq);
-    float sp, cp;
-    sincosf(phi, &sp, &cp);
-    f3 e = x * cp + q * sp;
-    x = unit(e + r);
-    phi = angle(x, r);
-}
+    __device__ __forceinline__ float phi() const { return full ? PI_F : atan2f(sp, cp); }
+};
 
 struct Pads {
     float sr, sa, cr, ca;
@@ -145,19 +166,24 @@ struct Caps {
     unsigned v[CRSH_MAX_LEVELS];
 };
 
-// A warp builds 32 consecutive level-1 nodes.  The 32 B rays are read
-// coalesced (lane = ray), the spheres merge as shuffle trees within B-lane
-// groups, and the unit directions go to shared memory node-major; then lane k
-// folds node k's cone ray by ray (eqs. 1-4), so 32 sequential folds run side
-// by side.
-constexpr int BL1_WARPS = 2;
-__global__ void __launch_bounds__(BL1_WARPS * 32) k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned B,
-                                                              unsigned L, Pads pads, LevelOut out, unsigned* counts,
-                                                              Caps caps) {
-    // node k's ray i at k (B + 1) + i: an odd stride, so the fold's reads
-    // (lane = node) hit 32 distinct banks
-    __shared__ float s_dir[BL1_WARPS][3][32 * 33];
-    __shared__ float4 s_sph[BL1_WARPS][32];
+// A warp builds 32 consecutive level-1 nodes (one block = one warp).  It
+// first copies the 32 B rays' origins and directions into shared memory with
+// every load in flight at once (coalesced, node-major rows of B + 1 floats),
+// then lane k builds node k alone: the sphere as the balanced pairwise tree of
+// eqs. 7-8 merged in place, the cone by the fold of eqs. 1-4.  The odd row
+// stride puts the 32 lanes' reads in 32 distinct banks.
+template <int B>
+__global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned L, Pads pads,
+                                                 LevelOut out, unsigned* counts, Caps caps) {
+    constexpr unsigned S = B + 1, W = 32 * S;
+    extern __shared__ float s_rows[];   // 7 x W floats: ox oy oz dx dy dz r
+    float* sox = s_rows;
+    float* soy = s_rows + W;
+    float* soz = s_rows + 2 * W;
+    float* sdx = s_rows + 3 * W;
+    float* sdy = s_rows + 4 * W;
+    float* sdz = s_rows + 5 * W;
+    float* srad = s_rows + 6 * W;
     const unsigned n = *n_ptr;
     const unsigned cnt = (n + B - 1) / B;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -173,57 +199,68 @@ __global__ void __launch_bounds__(BL1_WARPS * 32) k_build_l1(RaysIn rays, const 
         }
     }
     const unsigned lim = min(cnt, out.cap);
-    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, r = lane & (B - 1);
-    const unsigned stride = B + 1;
-    float* sdx = s_dir[warp][0];
-    float* sdy = s_dir[warp][1];
-    float* sdz = s_dir[warp][2];
-    const unsigned gw = blockIdx.x * BL1_WARPS + warp, nw = gridDim.x * BL1_WARPS;
-    for (unsigned j0 = gw * 32; j0 < lim; j0 += nw * 32) {
-        // load: B passes of 32 rays; pass t holds the 32 / B nodes from j0 + t (32 / B)
+    const unsigned lane = threadIdx.x;
+    for (unsigned j0 = blockIdx.x * 32; j0 < lim; j0 += gridDim.x * 32) {
+#pragma unroll
         for (unsigned t = 0; t < B; ++t) {
             const unsigned idx = t * 32 + lane;          // ray within this block of 32 nodes
-            const unsigned k = idx / B;                  // node within the block
-            const unsigned j = j0 + k;
-            const unsigned i = j0 * B + idx;             // sorted ray
-            const unsigned m = j < lim ? min(B, n - j * B) : 0u;
-            SC leaf;
-            leaf.c = mk3(0.f, 0.f, 0.f);
-            leaf.r = 0.0f;
-            leaf.x = mk3(1.f, 0.f, 0.f);
-            leaf.phi = 0.0f;
-            f3 d = mk3(1.f, 0.f, 0.f);
-            if (r < m) {
-                d = unit(mk3(rays.dx[i], rays.dy[i], rays.dz[i]));
-                leaf.c = mk3(rays.ox[i], rays.oy[i], rays.oz[i]);
+            const unsigned k = idx / B, r = idx % B;
+            const size_t i = (size_t)j0 * B + idx;       // sorted ray
+            if (j0 + k < lim && i < n) {
+                const unsigned a = k * S + r;
+                sox[a] = rays.ox[i];
+                soy[a] = rays.oy[i];
+                soz[a] = rays.oz[i];
+                sdx[a] = rays.dx[i];
+                sdy[a] = rays.dy[i];
+                sdz[a] = rays.dz[i];
             }
-            sdx[k * stride + r] = d.x;
-            sdy[k * stride + r] = d.y;
-            sdz[k * stride + r] = d.z;
-            // spheres: radius-0 leaves merged as a balanced tree (eqs. 7-8)
-            group_tree_merge<false>(leaf, r, m, B);
-            if (r == 0) s_sph[warp][k] = make_float4(leaf.c.x, leaf.c.y, leaf.c.z, leaf.r);
         }
         __syncwarp();
-        // cone: lane k folds node j0 + k in sorted ray order (eqs. 1-4)
         const unsigned j = j0 + lane;
         if (j < lim) {
-            const unsigned m = min(B, n - j * B);
-            const unsigned base = lane * stride;
-            f3 x = mk3(sdx[base], sdy[base], sdz[base]);
-            float phi = 0.0f;
-            for (unsigned i = 1; i < m; ++i) cone_add_ray(x, phi, mk3(sdx[base + i], sdy[base + i], sdz[base + i]));
-            const float4 sp = s_sph[warp][lane];
+            const unsigned m = min((unsigned)B, n - j * B);
+            const unsigned b = lane * S;
+            // sphere: radius-0 leaves, balanced pairwise tree in ray order (eqs. 7-8)
+            for (unsigned i = 0; i < m; ++i) srad[b + i] = 0.0f;
+            for (unsigned st = 1; st < m; st <<= 1) {
+                for (unsigned i = 0; i + st < m; i += 2 * st) {
+                    SC x, y;
+                    x.c = mk3(sox[b + i], soy[b + i], soz[b + i]);
+                    x.r = srad[b + i];
+                    y.c = mk3(sox[b + i + st], soy[b + i + st], soz[b + i + st]);
+                    y.r = srad[b + i + st];
+                    sphere_union(x, y);
+                    sox[b + i] = x.c.x;
+                    soy[b + i] = x.c.y;
+                    soz[b + i] = x.c.z;
+                    srad[b + i] = x.r;
+                }
+            }
+            // cone: the rays in sorted order (eqs. 1-4)
+            ConeFold f;
+            f.start(unit(mk3(sdx[b], sdy[b], sdz[b])));
+            for (unsigned i = 1; i < m; ++i) f.add(unit(mk3(sdx[b + i], sdy[b + i], sdz[b + i])));
             SC node;
-            node.c = mk3(sp.x, sp.y, sp.z);
-            node.r = sp.w;
-            node.x = x;
-            node.phi = phi;
+            node.c = mk3(sox[b], soy[b], soz[b]);
+            node.r = srad[b];
+            node.x = f.x;
+            node.phi = f.phi();
             pad_node(node, pads);
             store_node(out, j, node);
         }
         __syncwarp();
     }
+}
+
+template <int B>
+static void launch_build_l1(const RaysIn& ri, const uint32_t* n_rays, unsigned L, const Pads& pads,
+                            const LevelOut& o1, unsigned* counts, const Caps& caps, unsigned cap0, cudaStream_t s,
+                            const DeviceInfo& dev) {
+    const size_t smem = 7 * 32 * (B + 1) * sizeof(float);
+    const unsigned blocks = (cap0 + 31) / 32;
+    const unsigned grid = blocks < (unsigned)dev.sms * 32 ? (blocks ? blocks : 1) : dev.sms * 32;
+    k_build_l1<B><<<grid, 32, smem, s>>>(ri, n_rays, L, pads, o1, counts, caps);
 }
 
 __global__ void k_build_up(const float4* csph, const float4* ccone, const unsigned* counts, unsigned level_idx,
@@ -272,10 +309,14 @@ crsh_status build_launch(const crsh_rays* rays, const uint32_t* n_rays, const cr
     LevelOut o1{reinterpret_cast<float4*>(h->sphere[0]), reinterpret_cast<float4*>(h->cone[0]),
                 reinterpret_cast<float2*>(h->trig[0]), h->capacity[0]};
     // B lanes per node: blocks of 128 threads hold 128 / B nodes
-    // a warp per 32 nodes
-    const unsigned blocks1 = (unsigned)(((size_t)h->capacity[0] + 32 * BL1_WARPS - 1) / (32 * BL1_WARPS));
-    const unsigned grid1 = blocks1 < (unsigned)dev.sms * 16 ? (blocks1 ? blocks1 : 1) : dev.sms * 16;
-    k_build_l1<<<grid1, BL1_WARPS * 32, 0, s>>>(ri, n_rays, B, L, pads, o1, h->count, caps);
+    switch (B) {   // a warp per 32 nodes
+        case 2: launch_build_l1<2>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
+        case 4: launch_build_l1<4>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
+        case 8: launch_build_l1<8>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
+        case 16: launch_build_l1<16>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
+        case 32: launch_build_l1<32>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
+        default: return CRSH_ERR_INVALID_ARG;
+    }
     for (unsigned l = 1; l < L; ++l) {
         LevelOut o{reinterpret_cast<float4*>(h->sphere[l]), reinterpret_cast<float4*>(h->cone[l]),
                    reinterpret_cast<float2*>(h->trig[l]), h->capacity[l]};

@@ -81,6 +81,15 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// ---- asynchronous global -> shared copies (16-byte aligned both sides) ----
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// waits for every committed group but the newest one
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // ---- decoupled look-back (single-pass prefix across tiles) ---------------
 //
 // Tiles are handed out in increasing order (atomic counter), so every tile a

@@ -194,10 +194,12 @@ __device__ __forceinline__ unsigned pixel_rays(const crsh_gbuffer& g, unsigned p
     return cnt;
 }
 
+// Rays in generation order: one 32-byte record per ray, (ox, oy, oz, dx) and
+// (dy, dz, t_max, pixel bits), so the gather after the sort reads each ray as
+// one aligned 32-byte sector.  The type is not stored: it is the key's top
+// two bits (Section 3.3.2 layout).
 struct GenOut {
-    float *ox, *oy, *oz, *dx, *dy, *dz, *tmax;
-    uint8_t* type;
-    uint32_t* pixel;
+    float4* rec;     // 2 per ray
     uint32_t* key;   // generation-order keys
     uint32_t* val;   // = generation index
     uint32_t capacity;
@@ -205,11 +207,8 @@ struct GenOut {
 
 __device__ __forceinline__ void store_ray(const GenOut& o, unsigned pos, const GenRay& r, unsigned key,
                                           unsigned pixel) {
-    o.ox[pos] = r.o[0]; o.oy[pos] = r.o[1]; o.oz[pos] = r.o[2];
-    o.dx[pos] = r.d[0]; o.dy[pos] = r.d[1]; o.dz[pos] = r.d[2];
-    o.tmax[pos] = r.tmax;
-    o.type[pos] = r.type;
-    o.pixel[pos] = pixel;
+    o.rec[2 * (size_t)pos] = make_float4(r.o[0], r.o[1], r.o[2], r.d[0]);
+    o.rec[2 * (size_t)pos + 1] = make_float4(r.d[1], r.d[2], r.tmax, __uint_as_float(pixel));
     o.key[pos] = key;
     o.val[pos] = pos;
 }
@@ -531,11 +530,12 @@ struct SortedOut {
 
 __device__ __forceinline__ void copy_ray(const GenOut& gen, unsigned src, const SortedOut& out, unsigned i,
                                          unsigned key) {
-    out.ox[i] = gen.ox[src]; out.oy[i] = gen.oy[src]; out.oz[i] = gen.oz[src];
-    out.dx[i] = gen.dx[src]; out.dy[i] = gen.dy[src]; out.dz[i] = gen.dz[src];
-    out.tmax[i] = gen.tmax[src];
-    out.type[i] = gen.type[src];
-    out.pixel[i] = gen.pixel[src];
+    const float4 a = gen.rec[2 * (size_t)src], b = gen.rec[2 * (size_t)src + 1];
+    out.ox[i] = a.x; out.oy[i] = a.y; out.oz[i] = a.z;
+    out.dx[i] = a.w; out.dy[i] = b.x; out.dz[i] = b.y;
+    out.tmax[i] = b.z;
+    out.type[i] = (uint8_t)(key >> 30);
+    out.pixel[i] = __float_as_uint(b.w);
     out.ray_id[i] = src;
     out.keys[i] = key;
 }
@@ -545,13 +545,14 @@ __device__ __forceinline__ void copy_ray(const GenOut& gen, unsigned src, const 
 // (the skeleton: the sorted position of each chunk's first ray), then every
 // sorted position finds its chunk (k_gather).
 // ---------------------------------------------------------------------------
-constexpr int SCAN_BLOCK = 256, SCAN_ITEMS = 4, SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+constexpr int SCAN_BLOCK = 256, SCAN_ITEMS = 8, SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 
 __global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_pos(const uint32_t* kA, const uint32_t* vA, const uint32_t* kB,
                                                           const uint32_t* vB, const unsigned* plan,
                                                           const uint32_t* cbase, const unsigned* c_ptr,
-                                                          uint32_t* cpos, unsigned long long* status,
-                                                          unsigned* tile_ctr, crsh_counters* ctr) {
+                                                          uint32_t* cpos, uint32_t* sbase,
+                                                          unsigned long long* status, unsigned* tile_ctr,
+                                                          crsh_counters* ctr) {
     __shared__ unsigned s_tile;
     __shared__ unsigned s_warp[SCAN_BLOCK / 32];
     __shared__ unsigned long long s_prefix;
@@ -564,14 +565,16 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_pos(const uint32_t* kA, co
         if (tile >= n_tiles) break;
         // blocked: thread handles SCAN_ITEMS consecutive chunks
         const unsigned e0 = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
-        unsigned sz[SCAN_ITEMS], sum = 0;
+        unsigned sz[SCAN_ITEMS], cb[SCAN_ITEMS], sum = 0;
 #pragma unroll
         for (int i = 0; i < SCAN_ITEMS; ++i) {
             unsigned e = e0 + i;
             sz[i] = 0;
+            cb[i] = 0;
             if (e < C) {
                 unsigned c = sv[e];
-                sz[i] = cbase[c + 1] - cbase[c];
+                cb[i] = cbase[c];
+                sz[i] = cbase[c + 1] - cb[i];
             }
             sum += sz[i];
         }
@@ -591,7 +594,10 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_pos(const uint32_t* kA, co
 #pragma unroll
         for (int i = 0; i < SCAN_ITEMS; ++i) {
             unsigned e = e0 + i;
-            if (e < C) cpos[e] = run;
+            if (e < C) {
+                cpos[e] = run;
+                sbase[e] = cb[i];   // generation index of the chunk's first ray, in sorted order
+            }
             run += sz[i];
         }
     }
@@ -604,7 +610,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_pos(const uint32_t* kA, co
 // each ray finds its chunk by a binary search over the lanes, and the next
 // group starts from its first ray's chunk (the last ray's or the one after).
 __global__ void k_gather(int mode, GenOut gen, const uint32_t* kA, const uint32_t* vA, const uint32_t* kB,
-                         const uint32_t* vB, const unsigned* plan, const uint32_t* cbase, const uint32_t* cpos,
+                         const uint32_t* vB, const unsigned* plan, const uint32_t* sbase, const uint32_t* cpos,
                          const unsigned* c_ptr, const unsigned* n_ptr, SortedOut out) {
     const unsigned n = *n_ptr;
     const uint32_t* sv = (mode != 0 && plan[4]) ? vB : vA;
@@ -639,7 +645,7 @@ __global__ void k_gather(int mode, GenOut gen, const uint32_t* kA, const uint32_
         }
         const unsigned start = __shfl_sync(FULL, cl, l);
         const unsigned chunk = lo + l;
-        if (i < n) copy_ray(gen, cbase[sv[chunk]] + (i - start), out, i, sk[chunk]);
+        if (i < n) copy_ray(gen, sbase[chunk] + (i - start), out, i, sk[chunk]);
         // chunk of the next group's first ray: the last ray's chunk or the one after it
         const unsigned l31 = __shfl_sync(FULL, l, 31);
         const unsigned after = __shfl_sync(FULL, cl, min(l31 + 1, 31u));
@@ -668,7 +674,7 @@ struct Carve {
 
 struct HashWs {
     GenOut gen;
-    uint32_t *chK, *chV, *chBase, *chPos, *altK, *altV;
+    uint32_t *chK, *chV, *chBase, *chPos, *chSB, *altK, *altV;
     float* tables;
     // control region (zeroed per call)
     char* ctl_begin;
@@ -690,11 +696,7 @@ size_t table_floats() { return (1u << 13) * 2 + (1u << 13) / 8 * 2; }
 HashWs carve_hash(void* ws, uint32_t cap, uint32_t max_pixels) {
     Carve c{reinterpret_cast<char*>(ws)};
     HashWs w{};
-    w.gen.ox = c.take<float>(cap); w.gen.oy = c.take<float>(cap); w.gen.oz = c.take<float>(cap);
-    w.gen.dx = c.take<float>(cap); w.gen.dy = c.take<float>(cap); w.gen.dz = c.take<float>(cap);
-    w.gen.tmax = c.take<float>(cap);
-    w.gen.type = c.take<uint8_t>(cap);
-    w.gen.pixel = c.take<uint32_t>(cap);
+    w.gen.rec = c.take<float4>(2 * (size_t)cap);
     w.gen.key = c.take<uint32_t>(cap);
     w.gen.val = c.take<uint32_t>(cap);
     w.gen.capacity = cap;
@@ -702,6 +704,7 @@ HashWs carve_hash(void* ws, uint32_t cap, uint32_t max_pixels) {
     w.chV = c.take<uint32_t>(cap);
     w.chBase = c.take<uint32_t>((size_t)cap + 1);
     w.chPos = c.take<uint32_t>(cap);
+    w.chSB = c.take<uint32_t>(cap);
     w.altK = c.take<uint32_t>(cap);
     w.altV = c.take<uint32_t>(cap);
     w.tables = c.take<float>(table_floats());
@@ -791,7 +794,7 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
     if (compress) {
         unsigned tiles = (cap + SCAN_TILE - 1) / SCAN_TILE;
         unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
-        k_chunk_pos<<<grid, SCAN_BLOCK, 0, s>>>(kA, vA, w.altK, w.altV, w.plan, w.chBase, cnt_ptr, w.chPos,
+        k_chunk_pos<<<grid, SCAN_BLOCK, 0, s>>>(kA, vA, w.altK, w.altV, w.plan, w.chBase, cnt_ptr, w.chPos, w.chSB,
                                                  w.st_pos, &w.tile_ctr[6], ctr);
     }
     SortedOut so{out->ox, out->oy, out->oz, out->dx, out->dy, out->dz, out->tmax, out->type,
@@ -801,7 +804,7 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
         if (blocks > (unsigned)dev.sms * 4) blocks = dev.sms * 4;
         if (blocks == 0) blocks = 1;
         const int mode = !sort ? 0 : (compress ? 2 : 1);
-        k_gather<<<blocks, 256, 0, s>>>(mode, w.gen, kA, vA, w.altK, w.altV, w.plan, w.chBase, w.chPos, cnt_ptr,
+        k_gather<<<blocks, 256, 0, s>>>(mode, w.gen, kA, vA, w.altK, w.altV, w.plan, w.chSB, w.chPos, cnt_ptr,
                                         n_out, so);
     }
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;

@@ -24,6 +24,9 @@ struct TableSpec {
 };
 void tables_launch(const TableSpec& t, cudaStream_t s, const DeviceInfo& dev);
 
+// FP32 FMA throughput probe (probe.cu): returns the flops launched.
+unsigned long long fma_probe_launch(float* out, unsigned iters, unsigned blocks, cudaStream_t s);
+
 // One-sweep LSD radix sort of 32-bit (key, value) pairs (hash_sort.cu).
 struct RadixWs {
     unsigned* hist;      // 4 x 256, zeroed
