@@ -189,7 +189,7 @@ __device__ __forceinline__ unsigned lookback_thread32(unsigned* status, unsigned
                 set_status(ctr, CRSH_ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(32);
+            if (spins > 64) __nanosleep(32);   // short waits are polled, long ones back off
         }
     }
     st_relaxed32(&status[(size_t)tile * stride], LB32_INC | (excl + aggregate));

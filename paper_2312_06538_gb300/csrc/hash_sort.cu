@@ -84,15 +84,32 @@ __device__ __forceinline__ unsigned phi_bin(float x, float y, const float* T, un
     return q * Q + psi;
 }
 
+// bit b of x -> bit 2b (x < 2^16)
+__device__ __forceinline__ unsigned spread2(unsigned x) {
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+// bit b of x -> bit 3b (x < 2^10)
+__device__ __forceinline__ unsigned spread3(unsigned x) {
+    x &= 0x3FFu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+// Z-order code of the (theta, phi) bins: the low min(tb, pb) bits of both
+// interleaved (phi bit b at 2b, theta bit b at 2b + 1), the longer bin's
+// remaining bits above them.
 __device__ __forceinline__ unsigned interleave2(unsigned th, unsigned tb, unsigned ph, unsigned pb) {
-    unsigned code = 0, pos = 0, common = min(tb, pb);
-    for (unsigned b = 0; b < common; ++b) {
-        code |= ((ph >> b) & 1u) << pos++;
-        code |= ((th >> b) & 1u) << pos++;
-    }
-    for (unsigned b = common; b < pb; ++b) code |= ((ph >> b) & 1u) << pos++;
-    for (unsigned b = common; b < tb; ++b) code |= ((th >> b) & 1u) << pos++;
-    return code;
+    const unsigned common = min(tb, pb), m = (1u << common) - 1u;
+    return spread2(ph & m) | (spread2(th & m) << 1) | ((ph >> common) << (2 * common)) |
+           ((th >> common) << (2 * common));
 }
 
 __device__ __forceinline__ unsigned cell_coord(float o, float lo, float hi, unsigned bits) {
@@ -104,11 +121,9 @@ __device__ __forceinline__ unsigned cell_coord(float o, float lo, float hi, unsi
     return (unsigned)q;
 }
 
-__device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z, unsigned bits) {
-    unsigned c = 0;
-    for (unsigned b = 0; b < bits; ++b)
-        c |= ((x >> b) & 1u) << (3 * b) | ((y >> b) & 1u) << (3 * b + 1) | ((z >> b) & 1u) << (3 * b + 2);
-    return c;
+// Morton code of a cell (coordinates below 2^bits, bits <= 10)
+__device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z, unsigned) {
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
 }
 
 __device__ __forceinline__ unsigned ray_key(const GenRay& r, const HashDev& h) {
