@@ -155,13 +155,18 @@ constexpr unsigned LB32_VAL = (1u << 30) - 1;
 // one memory latency per LB32_WIN tiles.
 constexpr int LB32_WIN = 8;
 
-__device__ __forceinline__ unsigned lookback_thread32(unsigned* status, unsigned tile, unsigned stride,
-                                                      unsigned aggregate, crsh_counters* ctr) {
-    if (tile == 0) {
-        st_relaxed32(&status[0], LB32_INC | aggregate);
-        return 0;
-    }
-    st_relaxed32(&status[(size_t)tile * stride], LB32_AGG | aggregate);
+// Publishes a tile's own total (tile 0: already its inclusive prefix), so
+// successors can sum past it before it knows its own prefix.
+__device__ __forceinline__ void lookback32_publish(unsigned* status, unsigned tile, unsigned stride,
+                                                   unsigned aggregate) {
+    st_relaxed32(&status[(size_t)tile * stride], (tile == 0 ? LB32_INC : LB32_AGG) | aggregate);
+}
+
+// After lookback32_publish: the tile's exclusive prefix; publishes its
+// inclusive prefix.
+__device__ __forceinline__ unsigned lookback32_resolve(unsigned* status, unsigned tile, unsigned stride,
+                                                       unsigned aggregate, crsh_counters* ctr) {
+    if (tile == 0) return 0;
     unsigned excl = 0;
     unsigned spins = 0;
     long long k = (long long)tile - 1;   // next predecessor to consume
@@ -194,6 +199,12 @@ __device__ __forceinline__ unsigned lookback_thread32(unsigned* status, unsigned
     }
     st_relaxed32(&status[(size_t)tile * stride], LB32_INC | (excl + aggregate));
     return excl;
+}
+
+__device__ __forceinline__ unsigned lookback_thread32(unsigned* status, unsigned tile, unsigned stride,
+                                                      unsigned aggregate, crsh_counters* ctr) {
+    lookback32_publish(status, tile, stride, aggregate);
+    return lookback32_resolve(status, tile, stride, aggregate, ctr);
 }
 
 // Hands out tiles in increasing order; returns the tile in every thread.

@@ -398,7 +398,7 @@ static_assert(CMP_ITEMS * (CMP_BLOCK / 32) == 32, "one warp scans the per-warp c
 // ---------------------------------------------------------------------------
 // Section 3.3.4: radix sort (LSD, 8-bit digits, one sweep per digit).
 // ---------------------------------------------------------------------------
-constexpr int RS_BLOCK = 256, RS_WARPS = RS_BLOCK / 32, RS_KPT = 8, RS_TILE = RS_BLOCK * RS_KPT;
+constexpr int RS_BLOCK = 256, RS_WARPS = RS_BLOCK / 32, RS_KPT = 16, RS_TILE = RS_BLOCK * RS_KPT;
 
 __global__ void k_radix_hist(const uint32_t* key, const unsigned* n_ptr, unsigned* hist /* 4 x 256 */) {
     __shared__ unsigned s_h[4][256];
@@ -452,6 +452,13 @@ __global__ void k_radix_plan(const unsigned* hist, const unsigned* n_ptr, unsign
     }
 }
 
+// One LSD pass (8-bit digit) over tiles of RS_TILE keys taken in order from a
+// counter.  A tile is ranked in registers (per-warp match of equal digits,
+// counts in the warp's shared histogram, element order kept), its digit
+// totals are published at once (decoupled look-back), then it is sorted by
+// digit in shared memory while predecessors publish, and finally written out
+// in that local order: consecutive threads write consecutive positions of one
+// digit's run, so the stores are coalesced.
 __global__ void __launch_bounds__(RS_BLOCK) k_radix_pass(int pass, uint32_t* kA, uint32_t* vA, uint32_t* kB,
                                                          uint32_t* vB, const unsigned* n_ptr, const unsigned* offs,
                                                          const unsigned* plan, unsigned* status,
@@ -464,54 +471,83 @@ __global__ void __launch_bounds__(RS_BLOCK) k_radix_pass(int pass, uint32_t* kA,
     uint32_t* dv = (pl == 1) ? vB : vA;
     const unsigned shift = 8 * pass;
     __shared__ unsigned s_tile;
-    __shared__ unsigned s_wh[RS_WARPS][256];
-    __shared__ unsigned s_base[256];
+    __shared__ unsigned s_wh[RS_WARPS][256];   // per-warp digit counts, then their exclusive prefix over warps
+    __shared__ unsigned s_loc[256];            // tile-local start of each digit
+    __shared__ unsigned s_glob[256];           // global start of each digit minus its local start
+    __shared__ unsigned s_wsum[RS_WARPS];
+    __shared__ uint32_t s_key[RS_TILE];
+    __shared__ uint32_t s_val[RS_TILE];
     const unsigned n = *n_ptr;
     const unsigned n_tiles = (n + RS_TILE - 1) / RS_TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
     for (;;) {
         const unsigned tile = next_tile(tile_ctr, &s_tile);
         if (tile >= n_tiles) break;
         for (int i = lane; i < 256; i += 32) s_wh[warp][i] = 0;
         __syncwarp();
         unsigned key[RS_KPT], val[RS_KPT], rank[RS_KPT];
-        const unsigned base = tile * RS_TILE + warp * (32 * RS_KPT);
+        const unsigned t0 = tile * RS_TILE;
+        const unsigned cnt = min((unsigned)RS_TILE, n - t0);
+        const unsigned wbase = warp * (32 * RS_KPT);   // this warp's elements: wbase + r * 32 + lane
 #pragma unroll
         for (int r = 0; r < RS_KPT; ++r) {
-            unsigned e = base + r * 32 + lane;
-            bool valid = e < n;
-            key[r] = valid ? sk[e] : 0;
-            val[r] = valid ? sv[e] : 0;
-            unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u;
-            unsigned peers = __match_any_sync(FULL, d);
-            unsigned pre = valid ? s_wh[warp][d] : 0;
-            rank[r] = pre + __popc(peers & lanemask_lt());
+            const unsigned e = wbase + r * 32 + lane;
+            const bool valid = e < cnt;
+            key[r] = valid ? sk[t0 + e] : 0u;
+            val[r] = valid ? sv[t0 + e] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < RS_KPT; ++r) {
+            const bool valid = wbase + r * 32 + lane < cnt;
+            const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(FULL, d);
+            const unsigned pre = valid ? s_wh[warp][d] : 0u;
+            rank[r] = pre + __popc(peers & lt);
             __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) s_wh[warp][d] = pre + __popc(peers);
+            if (valid && (peers & lt) == 0) s_wh[warp][d] = pre + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
-        {   // thread = digit: exclusive over warps, tile total, look-back over tiles
-            const int d = threadIdx.x;
-            unsigned run = 0;
-            for (int w = 0; w < RS_WARPS; ++w) {
-                unsigned c = s_wh[w][d];
-                s_wh[w][d] = run;
-                run += c;
-            }
-            unsigned excl = lookback_thread32(status + d, tile, 256, run, ctr);
-            s_base[d] = offs[pass * 256 + d] + excl;
+        // thread = digit: prefix over warps, tile total published at once, then
+        // the exclusive scan over digits gives each digit's local start
+        const unsigned d = threadIdx.x;
+        unsigned tot = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            const unsigned c = s_wh[w][d];
+            s_wh[w][d] = tot;
+            tot += c;
         }
+        lookback32_publish(status + d, tile, 256, tot);
+        const unsigned inc = warp_incl_scan(tot);
+        if (lane == 31) s_wsum[warp] = inc;
         __syncthreads();
+        unsigned wpre = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) wpre += (w < warp) ? s_wsum[w] : 0u;
+        const unsigned loc = wpre + inc - tot;
+        s_loc[d] = loc;
+        __syncthreads();
+        // local sort by digit
 #pragma unroll
         for (int r = 0; r < RS_KPT; ++r) {
-            unsigned e = base + r * 32 + lane;
-            if (e < n) {
-                unsigned d = (key[r] >> shift) & 255u;
-                unsigned pos = s_base[d] + s_wh[warp][d] + rank[r];
-                dk[pos] = key[r];
-                dv[pos] = val[r];
+            if (wbase + r * 32 + lane < cnt) {
+                const unsigned dd = (key[r] >> shift) & 255u;
+                const unsigned lp = s_loc[dd] + s_wh[warp][dd] + rank[r];
+                s_key[lp] = key[r];
+                s_val[lp] = val[r];
             }
+        }
+        // global starts (predecessors have had the ranking time to publish)
+        const unsigned excl = lookback32_resolve(status + d, tile, 256, tot, ctr);
+        s_glob[d] = offs[pass * 256 + d] + excl - loc;
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < cnt; i += RS_BLOCK) {
+            const uint32_t k = s_key[i];
+            const unsigned pos = s_glob[(k >> shift) & 255u] + i;
+            dk[pos] = k;
+            dv[pos] = s_val[i];
         }
     }
 }
