@@ -217,7 +217,8 @@ def closest_traffic():
 
 def launches_per_step(levels: int, compress: bool) -> int:
     """Kernels of libcrsh.so launched by one pass (count of <<<>>> in the call sequence)."""
-    hash_sort = 1 + 1 + (1 if compress else 0) + 2 + 4 + (1 if compress else 0) + 1   # tables, gen, chunk, hist+plan, 4 passes, pos, gather
+    # tables, gen, chunk (which also counts the digits) or hist, plan, 4 passes, pos, gather
+    hash_sort = 1 + 1 + 1 + 1 + 4 + (1 if compress else 0) + 1
     build = levels
     traverse = 1 + 5 + 1 + 5 * (levels - 1) + 1   # mesh stage, top stage + its runs, 5 kernels per level, csr
     closest = 3

@@ -230,8 +230,11 @@ __device__ __forceinline__ void store_ray(const GenOut& o, unsigned pos, const G
 
 constexpr int GEN_BLOCK = 256;
 
-// One thread per pixel; stable trimming of empty slots by block scan plus
-// decoupled look-back across tiles.
+// PPT consecutive pixels per thread (the path launches PPT = 1: a blocked
+// layout with more pixels per thread measured slower); stable trimming of
+// empty slots by a block scan of the per-thread ray counts plus decoupled
+// look-back across tiles.
+template <int PPT>
 __global__ void __launch_bounds__(GEN_BLOCK) k_gen_gbuffer(crsh_gbuffer g, const float* lights, unsigned n_lights,
                                                            int cull, HashDev h, GenOut out, unsigned* n_out,
                                                            unsigned long long* status, unsigned* tile_ctr,
@@ -239,14 +242,17 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen_gbuffer(crsh_gbuffer g, const
     __shared__ unsigned s_tile;
     __shared__ unsigned s_warp[GEN_BLOCK / 32 + 1];
     __shared__ unsigned long long s_prefix;
-    const unsigned n_tiles = (g.n_pixels + GEN_BLOCK - 1) / GEN_BLOCK;
+    constexpr unsigned TILE = GEN_BLOCK * PPT;
+    const unsigned n_tiles = (g.n_pixels + TILE - 1) / TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         const unsigned tile = next_tile(tile_ctr, &s_tile);
         if (tile >= n_tiles) break;
-        const unsigned p = tile * GEN_BLOCK + threadIdx.x;
+        const unsigned p0 = tile * TILE + threadIdx.x * PPT;
         unsigned cnt = 0;
-        if (p < g.n_pixels) cnt = pixel_rays(g, p, lights, n_lights, cull != 0, [](const GenRay&) {});
+#pragma unroll
+        for (int j = 0; j < PPT; ++j)
+            if (p0 + j < g.n_pixels) cnt += pixel_rays(g, p0 + j, lights, n_lights, cull != 0, [](const GenRay&) {});
         // block exclusive scan
         unsigned inc = warp_incl_scan(cnt);
         if (lane == 31) s_warp[warp] = inc;
@@ -270,10 +276,15 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen_gbuffer(crsh_gbuffer g, const
         __syncthreads();
         unsigned long long pos = s_prefix + s_warp[warp] + inc - cnt;
         if (cnt) {
-            pixel_rays(g, p, lights, n_lights, cull != 0, [&](const GenRay& r) {
-                if (pos < out.capacity) store_ray(out, (unsigned)pos, r, ray_key(r, h), p);
-                ++pos;
-            });
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const unsigned p = p0 + j;
+                if (p < g.n_pixels)
+                    pixel_rays(g, p, lights, n_lights, cull != 0, [&](const GenRay& r) {
+                        if (pos < out.capacity) store_ray(out, (unsigned)pos, r, ray_key(r, h), p);
+                        ++pos;
+                    });
+            }
         }
     }
 }
@@ -327,16 +338,32 @@ void tables_launch(const TableSpec& t, cudaStream_t s, const DeviceInfo& dev) {
 // ---------------------------------------------------------------------------
 // Section 3.3.3: compression.  Head flag where the key differs from the
 // previous one; a stable compaction of the heads gives chunk key and base.
+// The same pass counts the chunk keys' digits for the radix sort (hist: 4 x
+// 256, zeroed); the top byte, which holds the ray type and few distinct
+// values, is aggregated per warp before its atomic.
 // ---------------------------------------------------------------------------
 constexpr int CMP_BLOCK = 256, CMP_ITEMS = 4, CMP_TILE = CMP_BLOCK * CMP_ITEMS;
 
+__device__ __forceinline__ void count_digits(unsigned (*s_h)[256], unsigned k, bool valid) {
+    if (valid) {
+        atomicAdd(&s_h[0][k & 255u], 1u);
+        atomicAdd(&s_h[1][(k >> 8) & 255u], 1u);
+        atomicAdd(&s_h[2][(k >> 16) & 255u], 1u);
+    }
+    const unsigned d3 = valid ? (k >> 24) : 256u;
+    const unsigned peers = __match_any_sync(FULL, d3);
+    if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&s_h[3][d3], (unsigned)__popc(peers));
+}
+
 __global__ void __launch_bounds__(CMP_BLOCK) k_chunk(const uint32_t* key, const unsigned* n_ptr, uint32_t* ckey,
                                                      uint32_t* cval, uint32_t* cbase, unsigned* c_out,
-                                                     unsigned long long* status, unsigned* tile_ctr,
+                                                     unsigned* hist, unsigned long long* status, unsigned* tile_ctr,
                                                      crsh_counters* ctr) {
     __shared__ unsigned s_tile;
     __shared__ unsigned s_cnt[CMP_ITEMS][CMP_BLOCK / 32];
     __shared__ unsigned long long s_prefix;
+    __shared__ unsigned s_h[4][256];
+    for (int i = threadIdx.x; i < 1024; i += CMP_BLOCK) (&s_h[0][0])[i] = 0;
     const unsigned n = *n_ptr;
     const unsigned n_tiles = (n + CMP_TILE - 1) / CMP_TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -390,7 +417,13 @@ __global__ void __launch_bounds__(CMP_BLOCK) k_chunk(const uint32_t* key, const 
                 cval[pos] = pos;
                 cbase[pos] = e;
             }
+            count_digits(s_h, f[i] ? k[i] : 0u, f[i]);
         }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 1024; i += CMP_BLOCK) {
+        const unsigned v = (&s_h[0][0])[i];
+        if (v) atomicAdd(&hist[i], v);
     }
 }
 static_assert(CMP_ITEMS * (CMP_BLOCK / 32) == 32, "one warp scans the per-warp counts");
@@ -562,9 +595,9 @@ size_t radix_status_words(uint32_t cap) {
 // rw.hist, rw.tile_ctr (4) and rw.status must be zero; rw.plan[4] tells which
 // buffer holds the result (0: A, 1: B).
 void radix_sort_launch(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, const unsigned* cnt_ptr, uint32_t cap,
-                       const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev) {
+                       const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev, bool counted) {
     const unsigned cap_tiles = (cap + RS_TILE - 1) / RS_TILE;
-    k_radix_hist<<<dev.sms * 2, 256, 0, s>>>(kA, cnt_ptr, rw.hist);
+    if (!counted) k_radix_hist<<<dev.sms * 2, 256, 0, s>>>(kA, cnt_ptr, rw.hist);
     k_radix_plan<<<1, 256, 0, s>>>(rw.hist, cnt_ptr, rw.offs, rw.plan, 1);
     const unsigned grid = cap_tiles < (unsigned)(dev.sms * 4) ? (cap_tiles ? cap_tiles : 1) : dev.sms * 4;
     const size_t rs_tiles = (size_t)cap_tiles + 1;
@@ -814,8 +847,8 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
     if (gb) {
         const unsigned tiles = (gb->n_pixels + GEN_BLOCK - 1) / GEN_BLOCK;
         const unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
-        k_gen_gbuffer<<<grid, GEN_BLOCK, 0, s>>>(*gb, lights, n_lights, (int)hp->shadow_cull, h, w.gen, n_out,
-                                                 w.st_gen, &w.tile_ctr[0], ctr);
+        k_gen_gbuffer<1><<<grid, GEN_BLOCK, 0, s>>>(*gb, lights, n_lights, (int)hp->shadow_cull, h, w.gen, n_out,
+                                                    w.st_gen, &w.tile_ctr[0], ctr);
     } else {
         unsigned blocks = (in->n + 255) / 256;
         if (blocks > (unsigned)persist) blocks = persist;
@@ -830,15 +863,15 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
     if (compress) {
         unsigned tiles = (cap + CMP_TILE - 1) / CMP_TILE;
         unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
-        k_chunk<<<grid, CMP_BLOCK, 0, s>>>(w.gen.key, n_out, w.chK, w.chV, w.chBase, &w.counts[0], w.st_chunk,
-                                           &w.tile_ctr[1], ctr);
+        k_chunk<<<grid, CMP_BLOCK, 0, s>>>(w.gen.key, n_out, w.chK, w.chV, w.chBase, &w.counts[0], w.hist,
+                                           w.st_chunk, &w.tile_ctr[1], ctr);
         kA = w.chK;
         vA = w.chV;
         cnt_ptr = &w.counts[0];
     }
     if (sort) {
         RadixWs rw{w.hist, w.offs, w.plan, &w.tile_ctr[2], w.st_radix};
-        radix_sort_launch(kA, vA, w.altK, w.altV, cnt_ptr, cap, rw, ctr, s, dev);
+        radix_sort_launch(kA, vA, w.altK, w.altV, cnt_ptr, cap, rw, ctr, s, dev, compress);
     } else {
         k_radix_plan<<<1, 256, 0, s>>>(w.hist, cnt_ptr, w.offs, w.plan, 0);
     }

@@ -36,8 +36,10 @@ struct RadixWs {
     unsigned* status;    // radix_status_words(cap), zeroed
 };
 size_t radix_status_words(uint32_t cap);
+// counted: rw.hist already holds the digit counts of the keys (their producer made them).
 void radix_sort_launch(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, const unsigned* cnt_ptr, uint32_t cap,
-                       const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev);
+                       const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev,
+                       bool counted = false);
 
 size_t hash_sort_workspace(uint32_t capacity, uint32_t max_pixels);
 crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, const float* lights, uint32_t n_lights,
