@@ -20,10 +20,16 @@ struct SC {
     float phi;
 };
 
+// Square root and quotient to a few ulps (special-function unit); the
+// padding applied after each merge covers their error.
+__device__ __forceinline__ float sqrt_fast(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
+
 // eqs. 7-8: sphere union, centre at the midpoint.
 __device__ __forceinline__ void sphere_union(SC& a, const SC& b) {
     f3 c = (a.c + b.c) * 0.5f;
-    float r = 0.5f * len(b.c - a.c) + fmaxf(a.r, b.r);
+    const f3 dc = b.c - a.c;
+    float r = 0.5f * sqrt_fast(dot(dc, dc)) + fmaxf(a.r, b.r);
     a.c = c;
     a.r = r;
 }
@@ -68,7 +74,7 @@ struct ConeFold {
         if (full) return;
         const float c = dot(x, r);
         const f3 w = cross(x, r);
-        const float s = sqrtf(dot(w, w));
+        const float s = sqrt_fast(dot(w, w));
         // inside iff theta <= phi: sin(phi - theta) >= 0, excluding phi - theta = -pi
         const float sd = sp * c - cp * s, cd = cp * c + sp * s;   // sin, cos of (phi - theta)
         if (sd > 0.0f || (sd == 0.0f && cd > 0.0f)) return;
@@ -79,13 +85,13 @@ struct ConeFold {
         }
         // turn the axis toward r by delta = (theta - phi) / 2: tan(delta) = sin(2 delta) / (1 + cos(2 delta))
         // = (1 - cos(2 delta)) / sin(2 delta), whichever side has no cancellation
-        const float td = cd >= 0.0f ? -sd / (1.0f + cd) : (1.0f - cd) / -sd;
+        const float td = cd >= 0.0f ? div_fast(-sd, 1.0f + cd) : div_fast(1.0f - cd, -sd);
         const float cdl = rsqrtf(1.0f + td * td), sdl = td * cdl;
-        const float is = 1.0f / s;
+        const float is = div_fast(1.0f, s);
         const f3 u = (r - x * c) * is;                              // unit normal to x toward r
         x = unit(x * cdl + u * sdl);
         // new spread (phi + theta) / 2: tan = sin(phi + theta) / (1 + cos(phi + theta)), or its other form
-        const float tp = cs >= 0.0f ? ss / (1.0f + cs) : (1.0f - cs) / ss;
+        const float tp = cs >= 0.0f ? div_fast(ss, 1.0f + cs) : div_fast(1.0f - cs, ss);
         cp = rsqrtf(1.0f + tp * tp);
         sp = tp * cp;
     }
