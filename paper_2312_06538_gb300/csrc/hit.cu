@@ -58,25 +58,26 @@ __device__ __forceinline__ unsigned long long hit_key(float t, unsigned tri) {
 }
 
 // Pre-test of a final test: a ray can only hit a triangle if its line passes
-// through the triangle's bounding sphere.  With v = c - o, s = v.d and
-// w = v - (s / |d|^2) d (the perpendicular from the line to the centre),
-// accept iff |w|^2 <= q + K s^2 / |d|^2, where q = 1.1 r^2 and K = 1.1e-7:
-// by (a + b)^2 <= 1.1 a^2 + 11 b^2 this holds whenever the distance is at
-// most r + 1e-4 x the distance along the ray, a slack far above the FP32
-// rounding of this test and of Moller-Trumbore's hit point even at grazing
-// incidence, so every triangle Moller-Trumbore would hit passes.  The brute
-// force takes the same pre-test, so both paths decide hits with one function.
-// id2 = 1 / |d|^2; a zero or non-finite direction rejects (as the test would).
-constexpr float PRETEST_K = 1.1e-7f;
-__device__ __forceinline__ bool near_line(float ox, float oy, float oz, float dx, float dy, float dz, float id2,
+// through the triangle's bounding sphere.  With v = c - o and s = v.d, the
+// squared distance from the centre to the line is |v|^2 - s^2 / |d|^2;
+// accept iff |v|^2 <= q + (1 + K) s^2 / |d|^2 with q = 1.1 r^2 and K = 2e-6.
+// Whenever the line passes within r + 1e-4 x the distance along the ray (a
+// slack far above the FP32 error of Moller-Trumbore's hit point, even at
+// grazing incidence; (a + b)^2 <= 1.1 a^2 + 11 b^2) this holds with room for
+// the FP32 rounding of |v|^2 and s^2 (a few ulps of |v|^2), so every
+// triangle Moller-Trumbore would hit passes.  The brute force takes the same
+// pre-test, so both paths decide hits with one function.
+// kid2 = (1 + K) / |d|^2; a zero direction makes s = 0 and 0 x inf a NaN, so
+// the test rejects, as Moller-Trumbore would (its determinant is 0).
+constexpr float PRETEST_K1 = 1.000002f;
+__device__ __forceinline__ bool near_line(float ox, float oy, float oz, float dx, float dy, float dz, float kid2,
                                           float4 C) {
     const float vx = C.x - ox, vy = C.y - oy, vz = C.z - oz;
+    const float vv = vx * vx + vy * vy + vz * vz;
     const float s = vx * dx + vy * dy + vz * dz;
-    const float tc = s * id2;
-    const float wx = vx - tc * dx, wy = vy - tc * dy, wz = vz - tc * dz;
-    const float w2 = wx * wx + wy * wy + wz * wz;
-    return w2 <= fmaf(s * PRETEST_K, tc, C.w);
+    return vv <= fmaf(s * s, kid2, C.w);
 }
+
 constexpr unsigned long long NO_HIT = ~0ull;
 
 struct RaysDev {
@@ -105,7 +106,7 @@ struct Ray7 {
 
 __device__ __forceinline__ Ray7 load_ray(const RaysDev& rays, unsigned i) {
     Ray7 r{rays.ox[i], rays.oy[i], rays.oz[i], rays.dx[i], rays.dy[i], rays.dz[i], rays.tmax[i], 0.f};
-    r.id2 = 1.0f / (r.dx * r.dx + r.dy * r.dy + r.dz * r.dz);
+    r.id2 = PRETEST_K1 / (r.dx * r.dx + r.dy * r.dy + r.dz * r.dz);
     return r;
 }
 
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(BF_BLOCK) k_brute(RaysDev rays, const unsigned
             dx = rays.dx[i]; dy = rays.dy[i]; dz = rays.dz[i];
             tmax = rays.tmax[i];
         }
-        const float id2 = 1.0f / (dx * dx + dy * dy + dz * dz);
+        const float id2 = PRETEST_K1 / (dx * dx + dy * dy + dz * dz);
         unsigned long long bk = NO_HIT;
         for (unsigned t0 = 0; t0 < n_tris; t0 += BF_BLOCK) {
             __syncthreads();
