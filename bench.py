@@ -462,6 +462,57 @@ def hbm_sweep(args, tiles_list=(1, 2, 4, 8, 16, 22), reps: int = 20):
         torch.cuda.empty_cache()
 
 
+def f3_timing(w, p, gstruct, lights, hp, flush, stream, dev, reps: int = 20):
+    """NEXT row f3 on the bench frame: primary visibility through the hierarchy (camera rays ->
+    build -> traverse -> closest hit -> G-buffer), and the next bounce (first-hit buffer of the
+    frame's secondary hits -> crsh_hash_sort)."""
+    import torch
+    from paper_2312_06538_gb300 import pipeline as pl
+    sh = stream.cuda_stream
+    npx = w.width * w.height
+    q = pl.Pipeline(w.scene, max_pixels=npx, n_lights=1, bundle=16, levels=4, ray_capacity=npx, device=dev)
+    _, bp = pl.workload_params(w)
+    cam = q.camera_struct(w.camera, w.width, w.height)
+    mat = torch.from_numpy(w.scene.tri_material.astype(np.int32)).to(dev)
+    gq, gqs = q.gbuffer_out(npx)
+    for _ in range(6):
+        q.run_primary(cam, bp, sh)
+        c = q.read_counters()
+        if c["status"] == 2 and c["needed_pairs"] > q.pair_capacity:
+            q.set_pair_capacity(int(1.25 * c["needed_pairs"]) + 1024)
+            continue
+        break
+
+    def primary():
+        q.run_primary(cam, bp, sh)
+        q.gbuffer_from_hits(mat, gqs, sh)
+    ms_p = time_path(primary, flush, stream, reps)
+    tri = q.hit_tri[:npx].cpu().numpy().view(np.int32)
+    agree = float((tri == w.primary_tri).mean())
+    # next bounce from the frame's secondary hits (p holds them after the main timing)
+    n = p.n()
+    gn, gns = p.gbuffer_out(n)
+    nb = pl.Pipeline(w.scene, max_pixels=n, n_lights=w.lights.shape[0], bundle=16, levels=4, device=dev,
+                     pair_capacity=1 << 16)
+    gstruct_n = nb.gbuffer_struct(gn)
+
+    def bounce():
+        p.gbuffer_from_hits(mat, gns, sh)
+        nb.hash_sort(gstruct_n, lights, hp, sh)
+    ms_b = time_path(bounce, flush, stream, reps)
+    n_next = nb.n()
+    out = {"primary": {"workload": f"{w.width}x{w.height} camera rays, B=16, L=4, through the hierarchy",
+                       "mrays_per_s": npx / (ms_p * 1e-3) / 1e6, "ms": ms_p,
+                       "tri_tests_per_ray": c["final_tests"] / npx,
+                       "same_triangle_as_fp64_raster": agree},
+           "next_bounce": {"rays_in": n, "rays_out": n_next, "ms": ms_b,
+                           "mrays_per_s": n_next / (ms_b * 1e-3) / 1e6,
+                           "what": "first-hit buffer of the secondary hits + hash/sort of the next bounce's rays"}}
+    del q, nb
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -599,6 +650,11 @@ def run_gpu(args, w):
             line["comparators"] = comparators(w, p, gstruct, lights, hp, bp, flush, stream, dev, n_rays)
         except Exception as e:  # a comparator must not cost the main line
             line["comparators"] = {"error": f"{type(e).__name__}: {e}"}
+    if not args.no_f3:
+        try:
+            line.update(f3_timing(w, p, gstruct, lights, hp, flush, stream, dev))
+        except Exception as e:
+            line["primary"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_batched:
         try:
             line["batched"] = batched_comparison(dev)
@@ -631,6 +687,7 @@ def main():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-f3", action="store_true", help="skip primary visibility / next bounce timing")
     ap.add_argument("--sweep", action="store_true",
                     help="hash/sort/build HBM sweep at 3M..70M rays (one JSON line per size) instead of the step")
     ap.add_argument("--sweep-tiles", type=int, nargs="*", default=None, help="sweep sizes in frame tiles")

@@ -57,6 +57,7 @@ typedef int crsh_status;
 #define CRSH_RAY_SHADOW     0
 #define CRSH_RAY_REFLECTION 1
 #define CRSH_RAY_REFRACTION 2
+#define CRSH_RAY_PRIMARY    3   /* camera rays from crsh_primary_rays; never hashed */
 
 #define CRSH_MAT_DIFFUSE 0
 #define CRSH_MAT_MIRROR  1
@@ -179,6 +180,66 @@ typedef struct {
     int32_t *tri;
     float *t, *u, *v;
 } crsh_hits;
+
+/* ---- Primary visibility, next bounce, mesh update (NEXT row f3) -------- */
+
+/* Pinhole camera.  Pixel (x, y) looks along fwd + sx right + sy up with
+ * sx = (2 (x + 0.5) / width - 1) tan_x and sy = (1 - 2 (y + 0.5) / height)
+ * tan_y (y = 0 is the top row). */
+typedef struct {
+    float eye[3];
+    float fwd[3], right[3], up[3];   /* orthonormal */
+    float tan_x, tan_y;              /* tangents of half the horizontal / vertical field of view */
+    uint32_t width, height;
+} crsh_camera;
+
+/* A first-hit buffer the library writes: the crsh_gbuffer layout, n entries
+ * (for a camera, n = width x height in row-major pixel order). */
+typedef struct {
+    float *px, *py, *pz, *nx, *ny, *nz, *ix, *iy, *iz;
+    uint32_t *material;
+    uint8_t *hit;
+    uint32_t n;
+} crsh_gbuffer_out;
+
+/* Camera rays for primary visibility through the same hierarchy path (they
+ * stand in for the rasterised G-buffer pass of Section 3.2).  Writes
+ * width x height rays to `out` in tile order: 8 x 8 pixel blocks in
+ * block-row-major order, Z-order inside a block (pixels outside the image
+ * skipped), so every aligned run of B <= 64 rays covers a compact tile and the
+ * rays need no hashing or sorting before crsh_build.  Origin = eye, direction
+ * = d / |d| for the d above (FP32, no contraction), t_max = +inf, type =
+ * CRSH_RAY_PRIMARY, ray_id = pixel = y width + x.  *n_out (device) =
+ * width x height.  out->capacity must hold width x height rays
+ * (CRSH_ERR_INVALID_ARG otherwise, as for a zero size). */
+crsh_status crsh_primary_rays(const crsh_camera *cam, crsh_rays *out, uint32_t *n_out, void *stream);
+
+/* First-hit buffer from closest hits (the G-buffer of Section 3.2, for
+ * primary rays, and the hit-point buffer next-bounce rays are generated from,
+ * Section 3.3.8).  For every ray i < *n_rays of `rays` with g = ray_id[i] <
+ * out->n: hits are read at g (crsh_closest_hit's order); on a hit, position =
+ * o + t d, normal = (v1 - v0) x (v2 - v0) / |.| turned to face the ray
+ * (n.d <= 0), incident = d, material = tri_material[tri], hit = 1; on a miss
+ * all zero except incident.  FP32 with a fixed operation order, no
+ * contraction.  Feeding `out` (as a crsh_gbuffer of width out->n, height 1)
+ * to crsh_hash_sort emits the next bounce's rays. */
+crsh_status crsh_gbuffer_from_hits(const crsh_rays *rays, const uint32_t *n_rays, const crsh_hits *hits,
+                                   const crsh_scene *scene, const uint32_t *tri_material,
+                                   crsh_gbuffer_out *out, void *stream);
+
+/* Writable vertices and mesh spheres of a scene. */
+typedef struct {
+    float *v0x, *v0y, *v0z, *v1x, *v1y, *v1z, *v2x, *v2y, *v2z;
+    float *mesh_sphere;              /* 4 floats per mesh */
+} crsh_scene_out;
+
+/* Per-frame bounding-volume update (Section 3.3.1): mesh m's vertices go
+ * through the affine map xf[12 m ..]: row-major 3 x 4 [A | b], v -> A v + b;
+ * its sphere's centre likewise and its radius scales by the Frobenius norm of
+ * A (at least the largest stretch), rounded up, so the sphere still encloses
+ * the moved mesh.  `in` and `out` may alias.  Call crsh_prepare_scene on the
+ * result before tracing it. */
+crsh_status crsh_transform_meshes(const crsh_scene *in, const float *xf, crsh_scene_out *out, void *stream);
 
 /* FP32 peak probe for roofline measurements (not a step of the method):
  * launches `blocks` x 256 threads, each running 8 independent FMA chains for

@@ -66,6 +66,10 @@ def lib() -> ctypes.CDLL:
         L.oracle_generate_rays.argtypes = [U32] + [P] * 11 + [U32, P, I] + [P] * 10
         L.oracle_hash.restype = I
         L.oracle_hash.argtypes = [I64] + [P] * 8 + [ctypes.POINTER(_HashParams), P]
+        L.oracle_primary_rays.restype = I64
+        L.oracle_primary_rays.argtypes = [P, U32, U32] + [P] * 7
+        L.oracle_gbuffer_from_hits.restype = None
+        L.oracle_gbuffer_from_hits.argtypes = [I64] + [P] * 21
         L.oracle_tables.restype = None
         L.oracle_tables.argtypes = [U32, U32, P, P]
         L.oracle_stable_sort.restype = None
@@ -325,3 +329,33 @@ def adjoint(rays: Dict[str, np.ndarray], hits, g_t, g_u, g_v, verts: np.ndarray)
     lib().oracle_adjoint(n, *[_p(r[k]) for k in ("ox", "oy", "oz", "dx", "dy", "dz")], _p(tri), _p(t), _p(u), _p(w),
                          _p(gt), _p(gu), _p(gv), v.shape[0], _p(v), _p(g_verts), _p(g_orig), _p(g_dir))
     return g_verts, g_orig, g_dir
+
+
+def primary_rays(camera: np.ndarray, width: int, height: int) -> Dict[str, np.ndarray]:
+    """Camera rays in tile order (NEXT row f3): camera = eye, fwd, right, up, tan_x, tan_y."""
+    cam = _c(np.asarray(camera)[:14], np.float32)
+    n = width * height
+    out = {k: np.empty(n, np.float32) for k in ("ox", "oy", "oz", "dx", "dy", "dz")}
+    pixel = np.empty(n, np.uint32)
+    got = lib().oracle_primary_rays(_p(cam), width, height, *[_p(out[k]) for k in ("ox", "oy", "oz", "dx", "dy", "dz")],
+                                    _p(pixel))
+    assert got == n
+    out["pixel"] = pixel
+    return out
+
+
+def gbuffer_from_hits(rays: Dict[str, np.ndarray], tri: np.ndarray, t: np.ndarray, verts: np.ndarray,
+                      tri_material: np.ndarray) -> Dict[str, np.ndarray]:
+    """First-hit buffer of rays (generation order) from their hits (tri, FP32 t)."""
+    r = {k: _c(rays[k], np.float32) for k in ("ox", "oy", "oz", "dx", "dy", "dz")}
+    n = r["ox"].shape[0]
+    tr, tt = _c(tri, np.int32), _c(t, np.float32)
+    v, m = _c(verts, np.float32), _c(tri_material, np.int32)
+    out = {k: np.empty(n, np.float32) for k in ("px", "py", "pz", "nx", "ny", "nz", "ix", "iy", "iz")}
+    out["material"] = np.empty(n, np.uint32)
+    out["hit"] = np.empty(n, np.uint8)
+    lib().oracle_gbuffer_from_hits(n, *[_p(r[k]) for k in ("ox", "oy", "oz", "dx", "dy", "dz")], _p(tr), _p(tt),
+                                   _p(v), _p(m), *[_p(out[k]) for k in ("px", "py", "pz", "nx", "ny", "nz", "ix",
+                                                                         "iy", "iz", "material", "hit")])
+    return out
+

@@ -771,3 +771,88 @@ void oracle_adjoint(int64_t n, const float* ox, const float* oy, const float* oz
         }
     }
 }
+
+/* ---- Primary visibility and first-hit buffers (NEXT row f3) ------------
+ * The paper rasterises the primary hits (Section 3.2); here camera rays go
+ * through the same traced path, and first-hit buffers are written from
+ * closest hits: the G-buffer for primary rays, and for secondary rays the
+ * hit points the next bounce is generated from (Section 3.3.8). */
+
+/* Camera rays of a w x h pinhole camera, cam = eye[3], fwd[3], right[3],
+ * up[3], tan_x, tan_y.  Pixel (x, y) looks along fwd + sx right + sy up with
+ * sx = (2 (x + 0.5) / w - 1) tan_x and sy = (1 - 2 (y + 0.5) / h) tan_y,
+ * normalised as d / sqrt(d.d); FP32, fixed order.  The rays are listed in
+ * tile order: 8 x 8 pixel blocks in block-row-major order and, inside a
+ * block, the pixels in Z order (x bit b at 2b, y bit b at 2b + 1), pixels
+ * outside the image skipped.  Returns the ray count. */
+int64_t oracle_primary_rays(const float* cam, uint32_t w, uint32_t h, float* ox, float* oy, float* oz, float* dx,
+                            float* dy, float* dz, uint32_t* pixel) {
+    int64_t n = 0;
+    for (uint32_t by = 0; by * 8 < h; ++by)
+        for (uint32_t bx = 0; bx * 8 < w; ++bx)
+            for (uint32_t z = 0; z < 64; ++z) {
+                uint32_t lx = 0, ly = 0;
+                for (int b = 0; b < 3; ++b) {
+                    lx |= ((z >> (2 * b)) & 1u) << b;
+                    ly |= ((z >> (2 * b + 1)) & 1u) << b;
+                }
+                uint32_t x = 8 * bx + lx, y = 8 * by + ly;
+                if (x >= w || y >= h) continue;
+                float sx = (2.0f * ((float)x + 0.5f)) / (float)w;
+                sx = (sx - 1.0f) * cam[12];
+                float sy = (2.0f * ((float)y + 0.5f)) / (float)h;
+                sy = (1.0f - sy) * cam[13];
+                float d[3];
+                for (int a = 0; a < 3; ++a) {
+                    float v = cam[3 + a] + sx * cam[6 + a];
+                    d[a] = v + sy * cam[9 + a];
+                }
+                float len = len3f(d[0], d[1], d[2]);
+                ox[n] = cam[0]; oy[n] = cam[1]; oz[n] = cam[2];
+                dx[n] = d[0] / len; dy[n] = d[1] / len; dz[n] = d[2] / len;
+                pixel[n] = y * w + x;
+                ++n;
+            }
+    return n;
+}
+
+/* First-hit buffer entry g of ray g = (o, d) with hit (tri[g], t[g]): on a
+ * hit, position o + t d, normal (v1 - v0) x (v2 - v0) normalised and turned
+ * to face the ray (n.d <= 0), incident d, material tri_material[tri]; on a
+ * miss zeros except the incident direction.  FP32, fixed order. */
+void oracle_gbuffer_from_hits(int64_t n, const float* ox, const float* oy, const float* oz, const float* dx,
+                              const float* dy, const float* dz, const int32_t* tri, const float* t,
+                              const float* verts, const int32_t* tri_material, float* px, float* py, float* pz,
+                              float* nx, float* ny, float* nz, float* ix, float* iy, float* iz, uint32_t* material,
+                              uint8_t* hit) {
+    for (int64_t g = 0; g < n; ++g) {
+        ix[g] = dx[g]; iy[g] = dy[g]; iz[g] = dz[g];
+        if (tri[g] < 0) {
+            px[g] = py[g] = pz[g] = 0.0f;
+            nx[g] = ny[g] = nz[g] = 0.0f;
+            material[g] = 0;
+            hit[g] = 0;
+            continue;
+        }
+        const float* v = verts + 9 * (int64_t)tri[g];
+        float tt = t[g];
+        float a = tt * dx[g]; px[g] = ox[g] + a;
+        a = tt * dy[g]; py[g] = oy[g] + a;
+        a = tt * dz[g]; pz[g] = oz[g] + a;
+        float e1x = v[3] - v[0], e1y = v[4] - v[1], e1z = v[5] - v[2];
+        float e2x = v[6] - v[0], e2y = v[7] - v[1], e2z = v[8] - v[2];
+        float p, q;
+        p = e1y * e2z; q = e1z * e2y; float cx = p - q;
+        p = e1z * e2x; q = e1x * e2z; float cy = p - q;
+        p = e1x * e2y; q = e1y * e2x; float cz = p - q;
+        float len = len3f(cx, cy, cz);
+        cx = cx / len; cy = cy / len; cz = cz / len;
+        float f = cx * dx[g];
+        f = f + cy * dy[g];
+        f = f + cz * dz[g];
+        if (f > 0.0f) { cx = -cx; cy = -cy; cz = -cz; }
+        nx[g] = cx; ny[g] = cy; nz[g] = cz;
+        material[g] = (uint32_t)tri_material[tri[g]];
+        hit[g] = 1;
+    }
+}

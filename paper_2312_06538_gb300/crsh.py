@@ -15,7 +15,7 @@ U64 = ctypes.c_uint64
 F32 = ctypes.c_float
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_IMPLEMENTED, ERR_BAD_INPUT = range(7)
-RAY_SHADOW, RAY_REFLECTION, RAY_REFRACTION = 0, 1, 2
+RAY_SHADOW, RAY_REFLECTION, RAY_REFRACTION, RAY_PRIMARY = 0, 1, 2, 3
 
 
 class crsh_gbuffer(ctypes.Structure):
@@ -73,6 +73,20 @@ class crsh_hits(ctypes.Structure):
     _fields_ = [("tri", P), ("t", P), ("u", P), ("v", P)]
 
 
+class crsh_camera(ctypes.Structure):
+    _fields_ = [("eye", F32 * 3), ("fwd", F32 * 3), ("right", F32 * 3), ("up", F32 * 3), ("tan_x", F32),
+                ("tan_y", F32), ("width", U32), ("height", U32)]
+
+
+class crsh_gbuffer_out(ctypes.Structure):
+    _fields_ = [(k, P) for k in ("px", "py", "pz", "nx", "ny", "nz", "ix", "iy", "iz", "material", "hit")] + \
+               [("n", U32)]
+
+
+class crsh_scene_out(ctypes.Structure):
+    _fields_ = [(k, P) for k in ("v0x", "v0y", "v0z", "v1x", "v1y", "v1z", "v2x", "v2y", "v2z", "mesh_sphere")]
+
+
 _lib = None
 
 # (name, restype, argtypes) of every exported entry point
@@ -81,6 +95,12 @@ SIGNATURES = [
     ("crsh_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("crsh_prepare_scene", ctypes.c_int, [ctypes.POINTER(crsh_scene), P]),
     ("crsh_hash_tables", ctypes.c_int, [U32, U32, P, P, P]),
+    ("crsh_primary_rays", ctypes.c_int, [ctypes.POINTER(crsh_camera), ctypes.POINTER(crsh_rays), P, P]),
+    ("crsh_gbuffer_from_hits", ctypes.c_int,
+     [ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_hits), ctypes.POINTER(crsh_scene), P,
+      ctypes.POINTER(crsh_gbuffer_out), P]),
+    ("crsh_transform_meshes", ctypes.c_int,
+     [ctypes.POINTER(crsh_scene), P, ctypes.POINTER(crsh_scene_out), P]),
     ("crsh_fma_probe", ctypes.c_int, [P, U32, U32, ctypes.POINTER(ctypes.c_ulonglong), P]),
     ("crsh_hash_sort_workspace", ctypes.c_size_t, [U32, U32]),
     ("crsh_hash_sort", ctypes.c_int,
@@ -150,6 +170,22 @@ def crsh_version() -> int:
 
 def crsh_prepare_scene(scene: crsh_scene, stream: int):
     _check("crsh_prepare_scene", load().crsh_prepare_scene(ctypes.byref(scene), P(stream)))
+
+
+def crsh_primary_rays(cam: crsh_camera, out: crsh_rays, n_out: int, stream: int):
+    _check("crsh_primary_rays", load().crsh_primary_rays(ctypes.byref(cam), ctypes.byref(out), P(n_out), P(stream)))
+
+
+def crsh_gbuffer_from_hits(rays: crsh_rays, n_rays: int, hits: crsh_hits, scene: crsh_scene, tri_material: int,
+                           out: crsh_gbuffer_out, stream: int):
+    _check("crsh_gbuffer_from_hits",
+           load().crsh_gbuffer_from_hits(ctypes.byref(rays), P(n_rays), ctypes.byref(hits), ctypes.byref(scene),
+                                         P(tri_material), ctypes.byref(out), P(stream)))
+
+
+def crsh_transform_meshes(scene: crsh_scene, xf: int, out: crsh_scene_out, stream: int):
+    _check("crsh_transform_meshes",
+           load().crsh_transform_meshes(ctypes.byref(scene), P(xf), ctypes.byref(out), P(stream)))
 
 
 def crsh_fma_probe(out: int, iters: int, blocks: int, stream: int) -> int:

@@ -78,6 +78,38 @@ crsh_status crsh_prepare_scene(const crsh_scene* scene, void* stream) {
     return prepare_scene_launch(scene, static_cast<cudaStream_t>(stream), dev);
 }
 
+crsh_status crsh_primary_rays(const crsh_camera* cam, crsh_rays* out, uint32_t* n_out, void* stream) {
+    if (!cam || !rays_ok(out) || !n_out || cam->width == 0 || cam->height == 0) return CRSH_ERR_INVALID_ARG;
+    if ((uint64_t)cam->width * cam->height > out->capacity) return CRSH_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if (!current_device(dev)) return CRSH_ERR_CUDA;
+    return primary_launch(cam, out, n_out, static_cast<cudaStream_t>(stream), dev);
+}
+
+crsh_status crsh_gbuffer_from_hits(const crsh_rays* rays, const uint32_t* n_rays, const crsh_hits* hits,
+                                   const crsh_scene* scene, const uint32_t* tri_material, crsh_gbuffer_out* out,
+                                   void* stream) {
+    if (!rays_ok(rays) || !n_rays || !hits || !hits->tri || !hits->t || !scene_ok(scene, false) || !tri_material ||
+        !out)
+        return CRSH_ERR_INVALID_ARG;
+    if (!out->px || !out->py || !out->pz || !out->nx || !out->ny || !out->nz || !out->ix || !out->iy || !out->iz ||
+        !out->material || !out->hit)
+        return CRSH_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if (!current_device(dev)) return CRSH_ERR_CUDA;
+    return gbuffer_from_hits_launch(rays, n_rays, hits, scene, tri_material, out, static_cast<cudaStream_t>(stream),
+                                    dev);
+}
+
+crsh_status crsh_transform_meshes(const crsh_scene* in, const float* xf, crsh_scene_out* out, void* stream) {
+    if (!scene_ok(in, false) || !xf || !out || !out->v0x || !out->v0y || !out->v0z || !out->v1x || !out->v1y ||
+        !out->v1z || !out->v2x || !out->v2y || !out->v2z || !out->mesh_sphere)
+        return CRSH_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if (!current_device(dev)) return CRSH_ERR_CUDA;
+    return transform_launch(in, xf, out, static_cast<cudaStream_t>(stream), dev);
+}
+
 crsh_status crsh_fma_probe(float* out, uint32_t iters, uint32_t blocks, unsigned long long* flops, void* stream) {
     if (!out || !flops || iters < 1 || blocks < 1 || blocks > (1u << 20)) return CRSH_ERR_INVALID_ARG;
     *flops = fma_probe_launch(out, iters, blocks, static_cast<cudaStream_t>(stream));

@@ -24,6 +24,15 @@ struct TableSpec {
 };
 void tables_launch(const TableSpec& t, cudaStream_t s, const DeviceInfo& dev);
 
+// Primary visibility, first-hit buffers, mesh update (primary.cu).
+crsh_status primary_launch(const crsh_camera* cam, crsh_rays* out, uint32_t* n_out, cudaStream_t s,
+                           const DeviceInfo& dev);
+crsh_status gbuffer_from_hits_launch(const crsh_rays* rays, const uint32_t* n_rays, const crsh_hits* hits,
+                                     const crsh_scene* sc, const uint32_t* tri_material, crsh_gbuffer_out* out,
+                                     cudaStream_t s, const DeviceInfo& dev);
+crsh_status transform_launch(const crsh_scene* in, const float* xf, crsh_scene_out* out, cudaStream_t s,
+                             const DeviceInfo& dev);
+
 // FP32 FMA throughput probe (probe.cu): returns the flops launched.
 unsigned long long fma_probe_launch(float* out, unsigned iters, unsigned blocks, cudaStream_t s);
 

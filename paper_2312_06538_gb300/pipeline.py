@@ -6,7 +6,7 @@ from __future__ import annotations
 
 import ctypes
 import math
-from typing import Dict, Optional
+from typing import Dict, Optional, Tuple
 
 import numpy as np
 import torch
@@ -210,6 +210,43 @@ class Pipeline:
                 raise C.CrshError("device status", c["status"])
             return c
         raise RuntimeError("pair capacity did not converge")
+
+    # ---- primary visibility and first-hit buffers (NEXT row f3) -----------
+    @staticmethod
+    def camera_struct(camera: np.ndarray, width: int, height: int) -> C.crsh_camera:
+        """camera = eye, fwd, right, up (3 each), tan_x, tan_y."""
+        c = np.asarray(camera, np.float64)
+        return C.crsh_camera((C.F32 * 3)(*c[0:3]), (C.F32 * 3)(*c[3:6]), (C.F32 * 3)(*c[6:9]),
+                             (C.F32 * 3)(*c[9:12]), float(c[12]), float(c[13]), int(width), int(height))
+
+    def primary(self, cam: C.crsh_camera, stream: int):
+        """Camera rays into the sorted-ray buffers (they need no hashing or sorting)."""
+        C.crsh_primary_rays(cam, self.rays, _ptr(self.n_rays), stream)
+
+    def run_primary(self, cam: C.crsh_camera, bp: C.crsh_build_params, stream: Optional[int] = None):
+        """Primary visibility through the hierarchy: camera rays -> build -> traverse -> closest hit."""
+        stream = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
+        self.primary(cam, stream)
+        self.build(bp, stream)
+        self.traverse(True, stream)
+        self.closest_hit(stream)
+
+    def gbuffer_out(self, n: int) -> Tuple[Dict[str, torch.Tensor], C.crsh_gbuffer_out]:
+        """A writable first-hit buffer of n entries."""
+        dev = self.device
+        g = {k: torch.empty(n, dtype=torch.float32, device=dev) for k in ("px", "py", "pz", "nx", "ny", "nz", "ix",
+                                                                         "iy", "iz")}
+        g["material"] = torch.empty(n, dtype=torch.int32, device=dev)
+        g["hit"] = torch.empty(n, dtype=torch.uint8, device=dev)
+        s = C.crsh_gbuffer_out(*[_ptr(g[k]) for k in ("px", "py", "pz", "nx", "ny", "nz", "ix", "iy", "iz",
+                                                     "material", "hit")], n)
+        s.keepalive = g
+        return g, s
+
+    def gbuffer_from_hits(self, tri_material: torch.Tensor, out: C.crsh_gbuffer_out, stream: Optional[int] = None):
+        """First-hit buffer of the traced rays, indexed by ray_id (asynchronous)."""
+        stream = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
+        C.crsh_gbuffer_from_hits(self.rays, _ptr(self.n_rays), self.hits, self.scene, _ptr(tri_material), out, stream)
 
     # ---- results (synchronising) ------------------------------------------
     def read_counters(self) -> dict:

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synthetic
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -630,3 +631,93 @@ def test_adjoint_accumulates_per_triangle_and_skips_misses():
     assert gd[0] == pytest.approx([0, 0, -5])
     # translating the triangle by +z moves t by +1: the three corner gradients sum to (0, 0, 1) per ray
     assert gv_[0].reshape(3, 3).sum(0) == pytest.approx([0, 0, 2])
+
+
+# --------------------------------------------------------------------------
+# NEXT row f3: camera rays and first-hit buffers
+# --------------------------------------------------------------------------
+
+def _cam(eye, fwd, right, up, tx, ty):
+    return np.array(list(eye) + list(fwd) + list(right) + list(up) + [tx, ty], np.float64)
+
+
+def test_primary_rays_cover_every_pixel_once_in_compact_tiles():
+    cam = _cam((0, 1, 5), (0, 0, -1), (1, 0, 0), (0, 1, 0), 0.6, 0.45)
+    for w, h in ((16, 8), (19, 13), (64, 64)):
+        r = oracle.primary_rays(cam, w, h)
+        assert np.array_equal(np.sort(r["pixel"]), np.arange(w * h))
+        x, y = r["pixel"] % w, r["pixel"] // w
+        full_w, full_h = (w // 8) * 8, (h // 8) * 8
+        for start in range(0, r["pixel"].size - 16 + 1, 16):
+            xs, ys = x[start:start + 16], y[start:start + 16]
+            if xs.max() < full_w and ys.max() < full_h:      # inside full blocks: a 4x4 square
+                assert xs.max() - xs.min() == 3 and ys.max() - ys.min() == 3
+        assert np.all(r["ox"] == np.float32(0)) and np.all(r["oz"] == np.float32(5))
+
+
+def test_primary_ray_directions_against_fp64():
+    fwd = np.array([0.3, -0.2, -1.0]); fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, [0, 1, 0]); right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    cam = _cam((1, 2, 3), fwd, right, up, 0.7, 0.5)
+    w, h = 24, 16
+    r = oracle.primary_rays(cam, w, h)
+    x, y = (r["pixel"] % w).astype(np.float64), (r["pixel"] // w).astype(np.float64)
+    c32 = cam.astype(np.float32).astype(np.float64)
+    sx = (2 * (x + 0.5) / w - 1) * c32[12]
+    sy = (1 - 2 * (y + 0.5) / h) * c32[13]
+    d = c32[3:6][None] + sx[:, None] * c32[6:9][None] + sy[:, None] * c32[9:12][None]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    got = np.stack([r["dx"], r["dy"], r["dz"]], 1).astype(np.float64)
+    assert np.abs(got - d).max() < 8 * np.finfo(np.float32).eps
+    # the corner pixel's angle to the axis matches the field of view
+    k = int(np.nonzero(r["pixel"] == 0)[0][0])
+    ang_x = math.atan(abs(np.dot(got[k], c32[6:9])) / np.dot(got[k], c32[3:6]))
+    assert abs(ang_x - math.atan((1 - 1 / w) * c32[12])) < 1e-6
+
+
+def test_odd_image_centre_ray_is_the_axis():
+    cam = _cam((0, 0, 0), (0, 0, -1), (1, 0, 0), (0, 1, 0), 0.5, 0.5)
+    r = oracle.primary_rays(cam, 9, 7)
+    k = int(np.nonzero(r["pixel"] == 3 * 9 + 4)[0][0])
+    assert (r["dx"][k], r["dy"][k], r["dz"][k]) == (0.0, 0.0, -1.0)
+
+
+def test_gbuffer_from_hits_worked_cases():
+    verts = np.array([[[0, 0, 0], [1, 0, 0], [0, 1, 0]],      # normal +z
+                      [[0, 0, 0], [0, 1, 0], [1, 0, 0]]],     # same plane, normal -z
+                     np.float32)
+    rays = rays_from([[0.25, 0.25, 1.0], [0.25, 0.25, 1.0], [0.25, 0.25, -2.0], [5, 5, 5]],
+                     [[0, 0, -1], [0, 0, -1], [0, 0, 1], [0, 0, 1]])
+    tri = np.array([0, 1, 0, -1], np.int32)
+    t = np.array([1.0, 1.0, 2.0, 0.0], np.float32)
+    g = oracle.gbuffer_from_hits(rays, tri, t, verts, np.array([7, 9], np.int32))
+    assert list(g["hit"]) == [1, 1, 1, 0]
+    for i in range(3):
+        assert (g["px"][i], g["py"][i], g["pz"][i]) == (0.25, 0.25, 0.0)
+    # normals face the incoming ray whatever the winding
+    assert (g["nx"][0], g["ny"][0], g["nz"][0]) == (0.0, 0.0, 1.0)
+    assert (g["nx"][1], g["ny"][1], g["nz"][1]) == (0.0, 0.0, 1.0)
+    assert (g["nx"][2], g["ny"][2], g["nz"][2]) == (0.0, 0.0, -1.0)
+    assert list(g["material"]) == [7, 9, 7, 0]
+    assert (g["ix"][3], g["iy"][3], g["iz"][3]) == (0.0, 0.0, 1.0) and g["px"][3] == 0 and g["nx"][3] == 0
+
+
+def test_gbuffer_from_hits_reproduces_the_raster_gbuffer():
+    """On config 1, the first-hit buffer of the camera rays, with the FP64 brute-force hits of
+    those rays, matches the software rasteriser's G-buffer: the same pixels hit the same
+    triangles (except where the FP32 ray direction decides an edge), with positions and normals
+    within FP32 rounding."""
+    w = synthetic.make(1)
+    r = oracle.primary_rays(w.camera, w.width, w.height)
+    tri, t, _, _ = oracle.bruteforce({**r, "tmax": np.full(r["ox"].shape, np.inf, np.float32)}, w.scene.verts)
+    g = oracle.gbuffer_from_hits(r, tri, t.astype(np.float32), w.scene.verts, w.scene.tri_material)
+    px = r["pixel"]
+    same = tri == w.primary_tri[px]
+    assert same.mean() > 0.995
+    both = same & (tri >= 0)
+    for k, kk in (("px", "px"), ("py", "py"), ("pz", "pz")):
+        assert np.allclose(g[k][both], w.gbuffer[kk][px][both], rtol=1e-5, atol=1e-5)
+    for k in ("nx", "ny", "nz"):
+        assert np.allclose(g[k][both], w.gbuffer[k][px][both], atol=1e-5)
+    assert np.array_equal(g["material"][both], w.gbuffer["material"][px][both])
