@@ -501,16 +501,69 @@ def f3_timing(w, p, gstruct, lights, hp, flush, stream, dev, reps: int = 20):
         nb.hash_sort(gstruct_n, lights, hp, sh)
     ms_b = time_path(bounce, flush, stream, reps)
     n_next = nb.n()
+    ms_s = time_path(lambda: p.shade(gstruct, lights, mat, sh), flush, stream, reps)
     out = {"primary": {"workload": f"{w.width}x{w.height} camera rays, B=16, L=4, through the hierarchy",
                        "mrays_per_s": npx / (ms_p * 1e-3) / 1e6, "ms": ms_p,
                        "tri_tests_per_ray": c["final_tests"] / npx,
                        "same_triangle_as_fp64_raster": agree},
            "next_bounce": {"rays_in": n, "rays_out": n_next, "ms": ms_b,
                            "mrays_per_s": n_next / (ms_b * 1e-3) / 1e6,
-                           "what": "first-hit buffer of the secondary hits + hash/sort of the next bounce's rays"}}
+                           "what": "first-hit buffer of the secondary hits + hash/sort of the next bounce's rays"},
+           "shade": {"pixels": npx, "rays": n, "ms": ms_s,
+                     "what": "crsh_shade: Lambert + hard shadows + one mirror/glass bounce from the frame's hits"}}
     del q, nb
     torch.cuda.empty_cache()
     return out
+
+
+# Table 4 of the paper (GTX TITAN, their scenes), quoted as context: total intersections
+TABLE4 = {"OFFICE": {"brute_force": 9133132168, "rah": 469683524, "crsh": 170070948},
+          "CORNELL": {"brute_force": 606911976, "rah": 72869648, "crsh": 53578192},
+          "SPONZA": {"brute_force": 17058578850, "rah": 632408864, "crsh": 405619896}}
+
+
+def paper_total(c: dict) -> int:
+    """Total intersections in the paper's convention: every level's B x parent-hit tests plus the
+    final B x level-1-hit tests (the identity that reproduces Table 4 from Tables 1-3)."""
+    return int(sum(c["tests_paper"]) + c["final_tests_paper"])
+
+
+def study(args):
+    """Row f4: the paper's evaluation shape (Section 4) on OFFICE-, CORNELL- and SPONZA-shaped
+    synthetic scenes at 512x512, hierarchy depth 2, B = 8: total intersections of CRSH (sorted,
+    whole-mesh culling), RAH (unsorted, no mesh culling) and the brute force, one JSON line per
+    scene."""
+    import synthetic
+    import torch
+    from paper_2312_06538_gb300 import pipeline as pl
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for name, make in synthetic.STUDY.items():
+        w = make()
+        row = {"study": name, "scene": w.name, "triangles": w.scene.n_tris}
+        for mode, sort, cull in (("crsh", True, True), ("rah", False, False)):
+            p = pl.workload_pipeline(w, device=dev)
+            hp, bp = pl.workload_params(w, sort=sort)
+            g = p.gbuffer_struct(p.gbuffer_to_device(w.gbuffer, dev))
+            lights = torch.from_numpy(w.lights).to(dev)
+            c = p.run_fit(g, lights, hp, bp, mesh_cull=cull)
+            tri = p.hits_host()[0]
+            types = np.bincount(p.sorted_rays()["type"], minlength=3)
+            row[mode] = {"total_isect": paper_total(c), "level_tests_paper": list(map(int, c["tests_paper"])),
+                         "level_hits": list(map(int, c["hits"])), "final_tests_paper": int(c["final_tests_paper"]),
+                         "final_hits": int(c["final_hits"]), "hit_rays": int((tri >= 0).sum())}
+            row["rays"] = int(c["rays"])
+            row["rays_by_type"] = {"shadow": int(types[0]), "reflection": int(types[1]), "refraction": int(types[2])}
+            del p
+            torch.cuda.empty_cache()
+        bf = row["rays"] * w.scene.n_tris
+        row["brute_force"] = {"total_isect": bf}
+        row["relative"] = {"crsh": row["crsh"]["total_isect"] / bf, "rah": row["rah"]["total_isect"] / bf,
+                           "crsh_vs_rah": row["crsh"]["total_isect"] / row["rah"]["total_isect"]}
+        t = TABLE4[name]
+        row["paper_table4_context"] = {"crsh_relative": t["crsh"] / t["brute_force"],
+                                       "rah_relative": t["rah"] / t["brute_force"],
+                                       "crsh_vs_rah": t["crsh"] / t["rah"]}
+        print(json.dumps(row), flush=True)
 
 
 def run_gpu(args, w):
@@ -692,8 +745,13 @@ def main():
                     help="hash/sort/build HBM sweep at 3M..70M rays (one JSON line per size) instead of the step")
     ap.add_argument("--sweep-tiles", type=int, nargs="*", default=None, help="sweep sizes in frame tiles")
     ap.add_argument("--sweep-reps", type=int, default=20)
+    ap.add_argument("--study", action="store_true",
+                    help="the paper-shaped depth-2, B=8 study (CRSH vs RAH vs brute force) instead of the step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
+    if args.study:
+        study(args)
+        return
     if args.sweep:
         if args.sweep_tiles:
             hbm_sweep(args, tiles_list=tuple(args.sweep_tiles), reps=args.sweep_reps)

@@ -241,6 +241,27 @@ typedef struct {
  * result before tracing it. */
 crsh_status crsh_transform_meshes(const crsh_scene *in, const float *xf, crsh_scene_out *out, void *stream);
 
+/* Shading accumulation (NEXT row f4; Section 3.3.8 turns the closest hits
+ * into shading but names no model, so this is a reading).  Grey level per
+ * pixel of `gb` (n_pixels entries, row-major), from the frame's secondary
+ * rays (`rays`, *n_rays of them, as crsh_hash_sort left them) and their hits
+ * (crsh_closest_hit's order):
+ *   no primary hit:  color = sky
+ *   else, material m (diffuse 0, mirror 1, glass 2) with albedo a = (0.8, 0.2,
+ *   0.1), reflectance k_r = (0, 0.8, 0.1), transmittance k_t = (0, 0, 0.8):
+ *   color = a (ambient + sum_k S_k) + k_r R + k_t T, summed in this order;
+ *   S_k = max(0, n . (-d)) for the shadow ray of light k if it reached the
+ *   light (no hit), else 0 (also 0 when no shadow ray was emitted); R, T =
+ *   for the reflection / refraction ray, a(hit material) (ambient + 0.5) on a
+ *   hit, sky on a miss, 0 when there is no such ray; ambient = 0.1, sky = 0.6.
+ * The shadow ray of light k is the one whose origin is lights[3k ..] (as
+ * crsh_hash_sort emits them).  FP32, fixed order, deterministic.
+ * cells: device scratch of n_pixels x (n_lights + 2) floats.  color: device,
+ * n_pixels floats. */
+crsh_status crsh_shade(const crsh_gbuffer *gb, const float *lights, uint32_t n_lights, const crsh_rays *rays,
+                       const uint32_t *n_rays, const crsh_hits *hits, const uint32_t *tri_material, float *cells,
+                       float *color, void *stream);
+
 /* FP32 peak probe for roofline measurements (not a step of the method):
  * launches `blocks` x 256 threads, each running 8 independent FMA chains for
  * 4 x iters steps, and writes one float per block to `out` (device, `blocks`

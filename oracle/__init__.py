@@ -70,6 +70,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_primary_rays.argtypes = [P, U32, U32] + [P] * 7
         L.oracle_gbuffer_from_hits.restype = None
         L.oracle_gbuffer_from_hits.argtypes = [I64] + [P] * 21
+        L.oracle_shade.restype = None
+        L.oracle_shade.argtypes = [U32] + [P] * 5 + [I64] + [P] * 8 + [U32, P]
         L.oracle_tables.restype = None
         L.oracle_tables.argtypes = [U32, U32, P, P]
         L.oracle_stable_sort.restype = None
@@ -358,4 +360,20 @@ def gbuffer_from_hits(rays: Dict[str, np.ndarray], tri: np.ndarray, t: np.ndarra
                                    _p(v), _p(m), *[_p(out[k]) for k in ("px", "py", "pz", "nx", "ny", "nz", "ix",
                                                                          "iy", "iz", "material", "hit")])
     return out
+
+
+def shade(gbuffer: Dict[str, np.ndarray], rays: Dict[str, np.ndarray], tri: np.ndarray, tri_material: np.ndarray,
+          n_lights: int) -> np.ndarray:
+    """Grey-level shading of the frame (NEXT row f4): rays in generation order (with type, light,
+    pixel), tri = their closest hits."""
+    npx = gbuffer["hit"].shape[0]
+    g = {k: _c(gbuffer[k], np.float32) for k in ("nx", "ny", "nz")}
+    mat, hit = _c(gbuffer["material"], np.uint32), _c(gbuffer["hit"], np.uint8)
+    r = {k: _c(rays[k], np.float32) for k in ("dx", "dy", "dz")}
+    ty, li, px = _c(rays["type"], np.uint8), _c(rays["light"], np.uint8), _c(rays["pixel"], np.uint32)
+    color = np.empty(npx, np.float32)
+    lib().oracle_shade(npx, _p(g["nx"]), _p(g["ny"]), _p(g["nz"]), _p(mat), _p(hit), ty.shape[0], _p(r["dx"]),
+                       _p(r["dy"]), _p(r["dz"]), _p(ty), _p(li), _p(px), _p(_c(tri, np.int32)),
+                       _p(_c(tri_material, np.int32)), int(n_lights), _p(color))
+    return color
 

@@ -856,3 +856,57 @@ void oracle_gbuffer_from_hits(int64_t n, const float* ox, const float* oy, const
         hit[g] = 1;
     }
 }
+
+/* ---- Shading accumulation (NEXT row f4; Section 3.3.8 accumulates shading
+ * after the final tests; the paper names no model, so this is a reading):
+ * grey level per pixel, Lambert with hard shadows plus one mirror/glass
+ * bounce.  Material m: albedo a = (0.8, 0.2, 0.1), reflectance k_r =
+ * (0, 0.8, 0.1), transmittance k_t = (0, 0, 0.8); ambient 0.1, sky 0.6.
+ *   no primary hit: sky
+ *   else a (ambient + sum_k S_k) + k_r R + k_t T, in this order, with
+ *   S_k = max(0, n . (-d)) for light k's shadow ray when it has no hit (0 if
+ *   it hit something or was not emitted), R / T = a(hit material) x
+ *   (ambient + 0.5) when the reflection / refraction ray hit, sky when it
+ *   missed, 0 when it was not emitted.  FP32, fixed order.
+ * Rays in generation order with their light index; tri[g] = closest hit of
+ * ray g (-1 = miss). */
+void oracle_shade(uint32_t n_pixels, const float* nx, const float* ny, const float* nz, const uint32_t* material,
+                  const uint8_t* hit, int64_t n_rays, const float* dx, const float* dy, const float* dz,
+                  const uint8_t* type, const uint8_t* light, const uint32_t* pixel, const int32_t* tri,
+                  const int32_t* tri_material, uint32_t n_lights, float* color) {
+    const float albedo[3] = {0.8f, 0.2f, 0.1f}, refl[3] = {0.0f, 0.8f, 0.1f}, trans[3] = {0.0f, 0.0f, 0.8f};
+    const float ambient = 0.1f, sky = 0.6f, bounce = 0.5f;
+    const size_t S = (size_t)n_lights + 2;
+    float* cell = (float*)calloc((size_t)n_pixels * S, sizeof(float));
+    for (int64_t g = 0; g < n_rays; ++g) {
+        uint32_t p = pixel[g];
+        if (type[g] == RAY_SHADOW) {
+            float v = 0.0f;
+            if (tri[g] < 0) {
+                float c = nx[p] * -dx[g];
+                c = c + ny[p] * -dy[g];
+                c = c + nz[p] * -dz[g];
+                v = c > 0.0f ? c : 0.0f;
+            }
+            cell[p * S + light[g]] = v;
+        } else {
+            float v = sky;
+            if (tri[g] >= 0) {
+                uint32_t hm = (uint32_t)tri_material[tri[g]];
+                v = albedo[hm <= 2 ? hm : 0] * (ambient + bounce);
+            }
+            cell[p * S + n_lights + (type[g] == RAY_REFRACTION ? 1 : 0)] = v;
+        }
+    }
+    for (uint32_t p = 0; p < n_pixels; ++p) {
+        if (!hit[p]) { color[p] = sky; continue; }
+        uint32_t m = material[p] <= 2 ? material[p] : 0;
+        float s = ambient;
+        for (uint32_t k = 0; k < n_lights; ++k) s = s + cell[p * S + k];
+        float col = albedo[m] * s;
+        col = col + refl[m] * cell[p * S + n_lights];
+        col = col + trans[m] * cell[p * S + n_lights + 1];
+        color[p] = col;
+    }
+    free(cell);
+}

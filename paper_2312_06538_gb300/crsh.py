@@ -101,6 +101,8 @@ SIGNATURES = [
       ctypes.POINTER(crsh_gbuffer_out), P]),
     ("crsh_transform_meshes", ctypes.c_int,
      [ctypes.POINTER(crsh_scene), P, ctypes.POINTER(crsh_scene_out), P]),
+    ("crsh_shade", ctypes.c_int,
+     [ctypes.POINTER(crsh_gbuffer), P, U32, ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_hits), P, P, P, P]),
     ("crsh_fma_probe", ctypes.c_int, [P, U32, U32, ctypes.POINTER(ctypes.c_ulonglong), P]),
     ("crsh_hash_sort_workspace", ctypes.c_size_t, [U32, U32]),
     ("crsh_hash_sort", ctypes.c_int,
@@ -186,6 +188,12 @@ def crsh_gbuffer_from_hits(rays: crsh_rays, n_rays: int, hits: crsh_hits, scene:
 def crsh_transform_meshes(scene: crsh_scene, xf: int, out: crsh_scene_out, stream: int):
     _check("crsh_transform_meshes",
            load().crsh_transform_meshes(ctypes.byref(scene), P(xf), ctypes.byref(out), P(stream)))
+
+
+def crsh_shade(gb: crsh_gbuffer, lights: int, n_lights: int, rays: crsh_rays, n_rays: int, hits: crsh_hits,
+               tri_material: int, cells: int, color: int, stream: int):
+    _check("crsh_shade", load().crsh_shade(ctypes.byref(gb), P(lights), n_lights, ctypes.byref(rays), P(n_rays),
+                                           ctypes.byref(hits), P(tri_material), P(cells), P(color), P(stream)))
 
 
 def crsh_fma_probe(out: int, iters: int, blocks: int, stream: int) -> int:

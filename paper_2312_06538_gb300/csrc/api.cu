@@ -110,6 +110,18 @@ crsh_status crsh_transform_meshes(const crsh_scene* in, const float* xf, crsh_sc
     return transform_launch(in, xf, out, static_cast<cudaStream_t>(stream), dev);
 }
 
+crsh_status crsh_shade(const crsh_gbuffer* gb, const float* lights, uint32_t n_lights, const crsh_rays* rays,
+                       const uint32_t* n_rays, const crsh_hits* hits, const uint32_t* tri_material, float* cells,
+                       float* color, void* stream) {
+    if (!gb || !gb->nx || !gb->ny || !gb->nz || !gb->material || !gb->hit || !rays_ok(rays) || !n_rays || !hits ||
+        !hits->tri || !tri_material || !cells || !color || (n_lights > 0 && !lights) || n_lights > 255)
+        return CRSH_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if (!current_device(dev)) return CRSH_ERR_CUDA;
+    return shade_launch(gb, lights, n_lights, rays, n_rays, hits, tri_material, cells, color,
+                        static_cast<cudaStream_t>(stream), dev);
+}
+
 crsh_status crsh_fma_probe(float* out, uint32_t iters, uint32_t blocks, unsigned long long* flops, void* stream) {
     if (!out || !flops || iters < 1 || blocks < 1 || blocks > (1u << 20)) return CRSH_ERR_INVALID_ARG;
     *flops = fma_probe_launch(out, iters, blocks, static_cast<cudaStream_t>(stream));

@@ -33,6 +33,11 @@ crsh_status gbuffer_from_hits_launch(const crsh_rays* rays, const uint32_t* n_ra
 crsh_status transform_launch(const crsh_scene* in, const float* xf, crsh_scene_out* out, cudaStream_t s,
                              const DeviceInfo& dev);
 
+// Shading accumulation (shade.cu).
+crsh_status shade_launch(const crsh_gbuffer* gb, const float* lights, uint32_t n_lights, const crsh_rays* rays,
+                         const uint32_t* n_rays, const crsh_hits* hits, const uint32_t* tri_material, float* cells,
+                         float* color, cudaStream_t s, const DeviceInfo& dev);
+
 // FP32 FMA throughput probe (probe.cu): returns the flops launched.
 unsigned long long fma_probe_launch(float* out, unsigned iters, unsigned blocks, cudaStream_t s);
 

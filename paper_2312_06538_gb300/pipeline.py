@@ -248,6 +248,19 @@ class Pipeline:
         stream = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
         C.crsh_gbuffer_from_hits(self.rays, _ptr(self.n_rays), self.hits, self.scene, _ptr(tri_material), out, stream)
 
+    def shade(self, gbuf: C.crsh_gbuffer, lights: Optional[torch.Tensor], tri_material: torch.Tensor,
+              stream: Optional[int] = None) -> torch.Tensor:
+        """Grey-level shading of the frame from its secondary rays and hits (asynchronous)."""
+        stream = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
+        npx = int(gbuf.n_pixels)
+        nl = 0 if lights is None else int(lights.shape[0])
+        cells = torch.empty(npx * (nl + 2), dtype=torch.float32, device=self.device)
+        color = torch.empty(npx, dtype=torch.float32, device=self.device)
+        C.crsh_shade(gbuf, _ptr(lights), nl, self.rays, _ptr(self.n_rays), self.hits, _ptr(tri_material),
+                     _ptr(cells), _ptr(color), stream)
+        color.keepalive = cells
+        return color
+
     # ---- results (synchronising) ------------------------------------------
     def read_counters(self) -> dict:
         torch.cuda.synchronize(self.device)

@@ -295,6 +295,62 @@ def config4_batches(n_batches: int = 32, lo: int = 1 << 11, hi: int = 1 << 20):
     return out
 
 
+# ---- scenes shaped like the paper's evaluation (Section 4.2), for the
+# depth-2, B = 8, 512x512 study of row f4.  The paper's models are not
+# available; these take their roles: OFFICE, an interior of many separate
+# meshes lit by one light (shadow rays); CORNELL, a small object inside six
+# mirrors (shadow and reflection rays); SPONZA, one undivided mesh (shadow
+# rays), which gives the whole-mesh spheres nothing to cull.
+
+def study_office(res: Optional[int] = None) -> Workload:
+    """OFFICE-shaped: a room with 20 icospheres(3), 12 tori 24x16 and 1 displaced sphere as
+    separate meshes (36,108 tris), all diffuse, one light, shadow rays only, B = 8, L = 2."""
+    w = h = res or 512
+    eye = np.array([0.0, 1.0, 3.5])
+    root, scene = _objects_scene(1101, 20, 3, 12, (24, 16), 1, -3, 3, 0.0, 0.0, "room", avoid=eye,
+                                 all_material=DIFFUSE)
+    lights = _lights(root, 1, scene.mesh_sphere[1:], 3.0, 2.0, 3.5)
+    cam = _camera(eye, (0, 0, 0), 60.0, w, h)
+    return _finish(f"OFFICE-shaped {w}x{h}, {scene.n_tris:,} tris in {scene.n_meshes} meshes, 1 light, "
+                   f"shadow rays (B=8, L=2)", w, h, scene, cam, lights, 8, 2, True, study_office.__doc__)
+
+
+def study_cornell(res: Optional[int] = None) -> Workload:
+    """CORNELL-shaped: an icosphere(2) and a torus 20x12 (800 tris, diffuse) inside a box whose
+    six walls are mirrors (12 tris), one light, shadow and reflection rays, B = 8, L = 2."""
+    w = h = res or 512
+    root = SplitMix64(1102)
+    sb = _SceneBuilder(1102)
+    sb.add(*meshes.room_box(2.0), MIRROR)
+    V, F = meshes.icosphere(2)
+    sb.add(V * 0.6 + np.array([-0.4, -0.9, 0.0]), F, DIFFUSE)
+    V, F = meshes.torus(20, 12, 0.5, 0.18)
+    sb.add(V @ meshes.random_rotation(root.substream(1)).T + np.array([0.6, -0.6, -0.3]), F, DIFFUSE)
+    scene = sb.finish()
+    lights = np.array([[0.0, 1.5, 0.5]], np.float32)
+    cam = _camera(np.array([0.0, 0.2, 1.8]), (0, -0.4, 0), 70.0, w, h)
+    return _finish(f"CORNELL-shaped {w}x{h}, {scene.n_tris:,} tris, six mirrors, 1 light, shadow + reflection "
+                   f"rays (B=8, L=2)", w, h, scene, cam, lights, 8, 2, True, study_cornell.__doc__)
+
+
+def study_sponza(res: Optional[int] = None) -> Workload:
+    """SPONZA-shaped: a room with 40 displaced icospheres(3) and 20 tori 24x16 merged into ONE mesh
+    (66,572 tris, no object subdivision), all diffuse, one light, shadow rays only, B = 8, L = 2."""
+    w = h = res or 512
+    eye = np.array([0.0, 1.0, 3.5])
+    root, parts = _objects_scene(1103, 0, 3, 20, (24, 16), 40, -3, 3, 0.0, 0.0, "room", avoid=eye,
+                                 all_material=DIFFUSE)
+    sb = _SceneBuilder(1103)
+    sb.parts.append((parts.verts, DIFFUSE))   # one mesh
+    scene = sb.finish()
+    lights = _lights(root, 1, parts.mesh_sphere[1:], 3.0, 2.0, 3.5)
+    cam = _camera(eye, (0, 0, 0), 60.0, w, h)
+    return _finish(f"SPONZA-shaped {w}x{h}, {scene.n_tris:,} tris in one mesh, 1 light, shadow rays "
+                   f"(B=8, L=2)", w, h, scene, cam, lights, 8, 2, True, study_sponza.__doc__)
+
+
+STUDY = {"OFFICE": study_office, "CORNELL": study_cornell, "SPONZA": study_sponza}
+
 CONFIGS = {1: config1, 2: config2, 3: config3, 5: config5}
 
 

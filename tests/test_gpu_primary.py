@@ -217,3 +217,29 @@ def test_mesh_update_moves_vertices_and_keeps_them_in_their_spheres():
     for m in range(M):
         pts = moved[first[m]:first[m + 1]].reshape(-1, 3)
         assert np.all(np.linalg.norm(pts - sph[m, :3], axis=1) <= sph[m, 3]), m
+
+
+def test_shading_matches_the_oracle_where_the_hits_agree():
+    """crsh_shade on a 96x96 config-2 frame: bit-exact against the oracle's shading for every
+    pixel whose secondary rays all hit the same triangles on both sides (the only input the
+    two do not share)."""
+    from paper_2312_06538_gb300 import pipeline as pl
+    w = synthetic.make(2, res=96)
+    p = pl.workload_pipeline(w)
+    hp, bp = pl.workload_params(w)
+    gs = p.gbuffer_struct(p.gbuffer_to_device(w.gbuffer))
+    lights = torch.from_numpy(w.lights).cuda()
+    p.run_fit(gs, lights, hp, bp)
+    mat = torch.from_numpy(w.scene.tri_material.astype(np.int32)).cuda()
+    color = p.shade(gs, lights, mat).cpu().numpy()
+    tri_g = p.hits_host()[0]
+    ref = oracle.run_crsh(w.gbuffer, w.lights, w.shadow_cull, w.hash_lo, w.hash_hi, w.scene, w.bundle,
+                          w.levels, w.build_pads())
+    tri_o = ref["hits"][0]
+    rc = oracle.shade(w.gbuffer, ref["rays"], tri_o, w.scene.tri_material, w.lights.shape[0])
+    px = ref["rays"]["pixel"]
+    bad = np.zeros(w.width * w.height, bool)
+    bad[px[tri_o != tri_g]] = True
+    assert (~bad).mean() > 0.99
+    assert np.array_equal(color[~bad].view(np.uint32), rc[~bad].view(np.uint32))
+    assert np.all(np.isfinite(color)) and color.min() >= 0.0

@@ -721,3 +721,33 @@ def test_gbuffer_from_hits_reproduces_the_raster_gbuffer():
     for k in ("nx", "ny", "nz"):
         assert np.allclose(g[k][both], w.gbuffer[k][px][both], atol=1e-5)
     assert np.array_equal(g["material"][both], w.gbuffer["material"][px][both])
+
+
+# --------------------------------------------------------------------------
+# NEXT row f4: shading accumulation (a stated reading; the paper names no model)
+# --------------------------------------------------------------------------
+
+def test_shade_worked_pixels():
+    s2 = math.sqrt(0.5)
+    # pixel 0: diffuse, normal +y, light 0 visible at 45 degrees, light 1 occluded
+    # pixel 1: mirror, normal +y, no shadow rays, reflection ray hits a diffuse triangle
+    # pixel 2: glass, reflection misses (sky), refraction hits glass
+    # pixel 3: background
+    gb = {"nx": np.array([0, 0, 0, 0], np.float32), "ny": np.array([1, 1, 1, 0], np.float32),
+          "nz": np.array([0, 0, 0, 0], np.float32), "material": np.array([0, 1, 2, 0], np.uint32),
+          "hit": np.array([1, 1, 1, 0], np.uint8)}
+    rays = {"dx": np.array([s2, 0, 0, 0, 0, 0], np.float32), "dy": np.array([-s2, -1, 1, 1, -1, -1], np.float32),
+            "dz": np.array([0, 0, 0, 0, 0, 0], np.float32),
+            "type": np.array([0, 0, 1, 1, 2, 0], np.uint8), "light": np.array([0, 1, 0, 0, 0, 0], np.uint8),
+            "pixel": np.array([0, 0, 1, 2, 2, 3], np.uint32)}
+    tri = np.array([-1, 5, 0, -1, 1, -1], np.int32)          # triangle 0 diffuse, 1 glass
+    tm = np.array([0, 2] + [0] * 4, np.int32)
+    c = oracle.shade(gb, rays, tri, tm, 2)
+    f = np.float32
+    assert c[0] == f(0.8) * (f(0.1) + f(s2) + f(0))          # n . (-d) = cos 45 degrees
+    assert c[1] == f(0.2) * f(0.1) + f(0.8) * (f(0.8) * (f(0.1) + f(0.5)))
+    assert c[2] == (f(0.1) * f(0.1) + f(0.1) * f(0.6)) + f(0.8) * (f(0.1) * (f(0.1) + f(0.5)))
+    assert c[3] == f(0.6)
+    # a back-facing light contributes nothing
+    rays["dy"][0] = np.float32(s2)
+    assert oracle.shade(gb, rays, tri, tm, 2)[0] == f(0.8) * f(0.1)
