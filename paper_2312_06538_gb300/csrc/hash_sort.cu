@@ -40,7 +40,7 @@ struct HashDev {
     const float* tanS;  // 2^spb / 8 entries
     const float* cosR;
     const float* tanR;
-    float lo[3], hi[3];
+    float lo[3], scale[3];   // origin-cell box and 2^cb / (hi - lo) per axis
     unsigned stb, spb, cb, tb, pb;
 };
 
@@ -112,9 +112,10 @@ __device__ __forceinline__ unsigned interleave2(unsigned th, unsigned tb, unsign
            ((th >> common) << (2 * common));
 }
 
-__device__ __forceinline__ unsigned cell_coord(float o, float lo, float hi, unsigned bits) {
+// scale = fl(2^bits / fl(hi - lo)), computed once per call on the host (IEEE
+// single precision there too, so the same bits)
+__device__ __forceinline__ unsigned cell_coord(float o, float lo, float scale, unsigned bits) {
     const float cells = (float)(1u << bits);
-    float scale = fd(cells, fs(hi, lo));
     float q = floorf(fm(fs(o, lo), scale));
     if (!(q >= 0.0f)) return 0;
     if (q > cells - 1.0f) return (1u << bits) - 1;
@@ -134,8 +135,8 @@ __device__ __forceinline__ unsigned ray_key(const GenRay& r, const HashDev& h) {
     }
     unsigned th = theta_bin(r.d[2], h.cosR, h.tb);
     unsigned ph = phi_bin(r.d[0], r.d[1], h.tanR, h.pb);
-    unsigned cell = morton3(cell_coord(r.o[0], h.lo[0], h.hi[0], h.cb), cell_coord(r.o[1], h.lo[1], h.hi[1], h.cb),
-                            cell_coord(r.o[2], h.lo[2], h.hi[2], h.cb), h.cb);
+    unsigned cell = morton3(cell_coord(r.o[0], h.lo[0], h.scale[0], h.cb), cell_coord(r.o[1], h.lo[1], h.scale[1], h.cb),
+                            cell_coord(r.o[2], h.lo[2], h.scale[2], h.cb), h.cb);
     return ((unsigned)r.type << 30) | (cell << (h.tb + h.pb)) | interleave2(th, h.tb, ph, h.pb);
 }
 
@@ -835,7 +836,13 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
     tables_launch(TableSpec{{tcosS, ttanS, tcosR, ttanR}, {BS, MS, BR, MR}, {0, 1, 0, 1}}, s, dev);
     HashDev h;
     h.cosS = tcosS; h.tanS = ttanS; h.cosR = tcosR; h.tanR = ttanR;
-    for (int a = 0; a < 3; ++a) { h.lo[a] = hp->lo[a]; h.hi[a] = hp->hi[a]; }
+    for (int a = 0; a < 3; ++a) {
+        // IEEE single-precision subtraction and division, rounded to nearest as on the device
+        volatile float ext = hp->hi[a] - hp->lo[a];
+        volatile float sc = (float)(1u << hp->sec_cell_bits) / ext;
+        h.lo[a] = hp->lo[a];
+        h.scale[a] = sc;
+    }
     h.stb = hp->shadow_theta_bits; h.spb = hp->shadow_phi_bits;
     h.cb = hp->sec_cell_bits; h.tb = hp->sec_theta_bits; h.pb = hp->sec_phi_bits;
 

@@ -351,6 +351,33 @@ def study_sponza(res: Optional[int] = None) -> Workload:
 
 STUDY = {"OFFICE": study_office, "CORNELL": study_cornell, "SPONZA": study_sponza}
 
+def tiled_gbuffer(w, tiles: int, seed: int = 77):
+    """`tiles` copies of the frame's G-buffer, each shifted (up to 0.05 per axis) and with
+    normals and incident directions turned by a small seeded rotation (up to 0.02 rad), so
+    keys stay spread like a larger frame's."""
+    rng = np.random.default_rng(seed)
+    parts = {k: [] for k in w.gbuffer}
+    for t in range(tiles):
+        shift = rng.uniform(-0.05, 0.05, 3).astype(np.float32) if t else np.zeros(3, np.float32)
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        ang = rng.uniform(0, 0.02) if t else 0.0
+        K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        R = (np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K).astype(np.float32)
+        g = w.gbuffer
+        P = np.stack([g["px"], g["py"], g["pz"]], 1) + shift
+        Nn = np.stack([g["nx"], g["ny"], g["nz"]], 1) @ R.T
+        I = np.stack([g["ix"], g["iy"], g["iz"]], 1) @ R.T
+        Nn /= np.linalg.norm(Nn, axis=1, keepdims=True).clip(1e-30)
+        I /= np.linalg.norm(I, axis=1, keepdims=True).clip(1e-30)
+        for k, col in (("px", P[:, 0]), ("py", P[:, 1]), ("pz", P[:, 2]), ("nx", Nn[:, 0]), ("ny", Nn[:, 1]),
+                       ("nz", Nn[:, 2]), ("ix", I[:, 0]), ("iy", I[:, 1]), ("iz", I[:, 2])):
+            parts[k].append(np.ascontiguousarray(col, np.float32))
+        parts["material"].append(g["material"])
+        parts["hit"].append(g["hit"])
+    return {k: np.concatenate(v) for k, v in parts.items()}
+
+
 CONFIGS = {1: config1, 2: config2, 3: config3, 5: config5}
 
 

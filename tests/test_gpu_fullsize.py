@@ -125,3 +125,33 @@ def test_c3_sampled_hits_and_gpu_bruteforce(c3):
     p.bruteforce()
     for x, y in zip(hits, p.hits_host()):
         assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+
+
+@pytest.mark.parametrize("compress", [True, False])
+def test_sort_at_12m_rays_bit_exact(compress):
+    """The hash/sort path at the size of the HBM sweep (4 perturbed tiles of the config-3 frame,
+    12.8 M rays, 3,100 radix tiles per pass): keys and order bit-exact against the oracle's
+    generation, hash and stable sort, with and without compression."""
+    from paper_2312_06538_gb300 import pipeline as pl
+    w = synthetic.make(3)
+    g = synthetic.tiled_gbuffer(w, 4)
+    npx = g["hit"].shape[0]
+    p = pl.Pipeline(w.scene, max_pixels=npx, n_lights=w.lights.shape[0], bundle=16, levels=4,
+                    ray_capacity=npx * 4, pair_capacity=1 << 16, device="cuda")
+    hp = pl.hash_params(w.hash_lo, w.hash_hi, shadow_cull=w.shadow_cull, compress=compress)
+    gs = p.gbuffer_struct(p.gbuffer_to_device(g))
+    p.hash_sort(gs, torch.from_numpy(w.lights).cuda(), hp, torch.cuda.current_stream().cuda_stream)
+    c = p.read_counters()
+    assert c["status"] == 0
+    rays = oracle.generate_rays(g, w.lights, w.shadow_cull)
+    keys = oracle.hash_keys(rays, w.hash_lo, w.hash_hi)
+    perm = oracle.stable_sort(keys)
+    n = p.n()
+    assert n == keys.shape[0] > 12_000_000
+    got = p.sorted_rays()
+    assert np.array_equal(got["keys"], keys[perm])
+    assert np.array_equal(got["ray_id"], perm.astype(np.uint32))
+    for k in ("ox", "dx", "tmax"):
+        assert np.array_equal(got[k].view(np.uint32), rays[k][perm].view(np.uint32)), k
+    if compress:
+        assert c["chunks"] == oracle.chunk_count(keys)
