@@ -113,7 +113,7 @@ __device__ __forceinline__ Ray7 load_ray(const RaysDev& rays, unsigned i) {
 
 __device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
-constexpr unsigned CH_PAIRS = 256;   // pairs per work chunk
+constexpr unsigned CH_PAIRS = 128;   // pairs per work chunk
 
 // Warps take chunks of CH_PAIRS consecutive pairs of the node-sorted pair
 // list from an atomic counter (the cost of a chunk depends on how many nodes
@@ -247,6 +247,17 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
                 }
             }
             __syncwarp();   // buffer buf is refilled two groups on
+            if (has2) {   // warm L1 with the rays of every node that starts in the window two groups on
+                const unsigned prev = __shfl_up_sync(FULL, pw2, 1);
+                if (pw2 != 0xffffffffu && (lane == 0 || prev != pw2)) {
+                    const unsigned nr = pw2 * B;   // the node's B rays share one 64-byte-aligned span per array
+                    if (nr < N) {
+                        prefetch_l1(rays.ox + nr); prefetch_l1(rays.oy + nr); prefetch_l1(rays.oz + nr);
+                        prefetch_l1(rays.dx + nr); prefetch_l1(rays.dy + nr); prefetch_l1(rays.dz + nr);
+                        prefetch_l1(rays.tmax + nr);
+                    }
+                }
+            }
             if (!has1) break;
             if (nnode != cur) {
                 flush_best<H>(k0, v0, sidx, ray0, best);
