@@ -69,6 +69,7 @@ struct TvCtl {
 //   finish(total, tests_paper_base)    stage totals, written by the last tile
 template <class Op>
 __global__ void __launch_bounds__(TV_BLOCK) k_compact(Op op, TvCtl ctl) {
+    pdl_wait();
     __shared__ unsigned s_tile;
     __shared__ unsigned s_cnt[TV_ITEMS][TV_BLOCK / 32];
     __shared__ unsigned long long s_prefix;
@@ -250,6 +251,7 @@ struct RunOut {
 template <class Parents>
 __global__ void __launch_bounds__(1024) k_unit_scan(Parents par, StageBuf sb, crsh_counters* ctr, int level_idx,
                                                     unsigned B_paper) {
+    pdl_wait();
     __shared__ unsigned long long s_w[32][4];
     __shared__ unsigned long long s_tot[4];
     const unsigned n = par.count();
@@ -445,6 +447,7 @@ __device__ __forceinline__ float4 chunk_sphere(float4 ts, bool valid) {
 // (its word is 0) and only the children that accept it run the 32-lane tests.
 template <class Parents>
 __global__ void __launch_bounds__(256, 5) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
+    pdl_wait();
     const WorkSplit ws(sb.totals[0], sb.work + 0, 16u);
     const int lane = threadIdx.x & 31;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -521,6 +524,7 @@ __device__ __forceinline__ void block_range(unsigned O, unsigned& w0, unsigned& 
 // Accepted pairs per scan block (contiguous ranges of ballot words; ranges
 // start on multiples of SC_TILE words, so 16-byte loads are aligned).
 __global__ void __launch_bounds__(SC_BLOCK) k_reduce(StageBuf sb) {
+    pdl_wait();
     const unsigned O = sb.totals[1];
     unsigned w0, w1;
     block_range(O, w0, w1);
@@ -546,6 +550,7 @@ __global__ void __launch_bounds__(SC_BLOCK) k_reduce(StageBuf sb) {
 // pair of word w; pos[O] = total; the stage's pair count and counters.
 __global__ void __launch_bounds__(SC_BLOCK) k_wordscan(StageBuf sb, PairOut out, crsh_counters* ctr,
                                                        int level_idx) {
+    pdl_wait();
     __shared__ unsigned long long s_pre;
     __shared__ unsigned s_w[SC_BLOCK / 32 + 1];
     const unsigned O = sb.totals[1];
@@ -639,6 +644,7 @@ struct EmitLoads {
 
 template <class Parents>
 __global__ void __launch_bounds__(256) k_emit(Parents par, StageBuf sb, PairOut out, RunOut runs) {
+    pdl_wait();
     const WorkSplit ws(sb.totals[0], sb.work + 1, 32u);
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -682,6 +688,7 @@ __global__ void __launch_bounds__(256) k_emit(Parents par, StageBuf sb, PairOut 
 // Runs of a node-sorted pair list: the pair that opens a node's run writes its
 // start, the pair that closes it writes its end (nodes without pairs keep 0, 0).
 __global__ void k_runs_from_pairs(const uint32_t* node, const unsigned* p_count, RunOut runs) {
+    pdl_wait();
     const unsigned P = *p_count;
     for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
         const uint32_t n = node[q];
@@ -697,6 +704,7 @@ __global__ void k_runs_from_pairs(const uint32_t* node, const unsigned* p_count,
 // column.
 __global__ void k_runs_to_csr(RunOut runs, const uint32_t* node, const unsigned* n_count, const unsigned* p_count,
                               unsigned long long cap, uint32_t* off) {
+    pdl_wait();
     const unsigned n = *n_count;
     const unsigned total = (unsigned)min((unsigned long long)*p_count, cap);
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) {
@@ -827,11 +835,11 @@ static void run_stage(const Parents& par, const TvWs& w, unsigned stage, const f
     // persistent grids: the count and emit passes claim unit batches
     const unsigned gc = dev.sms * resident_blocks(k_count<Parents>, 256, dev);
     const unsigned ge = dev.sms * resident_blocks(k_emit<Parents>, 256, dev);
-    k_unit_scan<Parents><<<1, 1024, 0, s>>>(par, sb, ctr, level_idx, B_paper);
-    k_count<Parents><<<gc, 256, 0, s>>>(par, sb, tsph);
-    k_reduce<<<sg, SC_BLOCK, 0, s>>>(sb);
-    k_wordscan<<<sg, SC_BLOCK, 0, s>>>(sb, out, ctr, level_idx);
-    k_emit<Parents><<<ge, 256, 0, s>>>(par, sb, out, runs);
+    launch_pdl(k_unit_scan<Parents>, 1, 1024, 0, s, par, sb, ctr, level_idx, B_paper);
+    launch_pdl(k_count<Parents>, gc, 256, 0, s, par, sb, tsph);
+    launch_pdl(k_reduce, sg, SC_BLOCK, 0, s, sb);
+    launch_pdl(k_wordscan, sg, SC_BLOCK, 0, s, sb, out, ctr, level_idx);
+    launch_pdl(k_emit<Parents>, ge, 256, 0, s, par, sb, out, runs);
 }
 
 crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const crsh_traverse_params* tp,
@@ -861,13 +869,13 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     MeshOp mop{level_nodes(L), h->count + (L - 1), reinterpret_cast<const float4*>(sc->mesh_sphere),
                sc->mesh_first_tri, sc->n_meshes, (int)tp->mesh_cull,
                PairOut{w.mpN, w.mpM, &w.counts[0], (unsigned long long)h->capacity[L - 1] * sc->n_meshes}, ctr};
-    k_compact<MeshOp><<<dev.sms * 2, TV_BLOCK, 0, s>>>(mop, TvCtl{w.st_mesh, &w.tile_ctr[0], ctr, -1});
+    launch_pdl(k_compact<MeshOp>, dev.sms * 2, TV_BLOCK, 0, s, mop, TvCtl{w.st_mesh, &w.tile_ctr[0], ctr, -1});
     // top level: triangles of the accepted meshes
     TopParents top{w.mpN, w.mpM, &w.counts[0], sc->mesh_first_tri, level_nodes(L)};
     run_stage(top, w, 0u, tsph, pairs_of(L), w.runs[L - 1], ctr, (int)L - 1, 0u, dev, s);
     {
         const PairOut tp_out = pairs_of(L);
-        k_runs_from_pairs<<<dev.sms * 4, 256, 0, s>>>(tp_out.node, tp_out.count, w.runs[L - 1]);
+        launch_pdl(k_runs_from_pairs, dev.sms * 4, 256, 0, s, tp_out.node, tp_out.count, w.runs[L - 1]);
     }
     // levels L-1 .. 1: parents are the nodes of level l+1 and their pair runs
     for (unsigned l = L - 1; l >= 1; --l) {
@@ -878,8 +886,8 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     }
     {
         const unsigned blocks = (h->capacity[0] + 256) / 256;
-        k_runs_to_csr<<<std::min<unsigned>(blocks, dev.sms * 8), 256, 0, s>>>(w.runs[0], out->node, h->count,
-                                                                              out->count, cap, out->node_offsets);
+        launch_pdl(k_runs_to_csr, std::min<unsigned>(blocks, dev.sms * 8), 256, 0, s, w.runs[0], out->node,
+                   (const unsigned*)h->count, (const unsigned*)out->count, cap, out->node_offsets);
     }
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
 }
