@@ -345,8 +345,8 @@ size_t crsh_closest_hit_workspace(uint32_t ray_capacity);
 /* Section 3.3.8.  For every level-1 pair (n, t) and every ray of n:
  * Moller-Trumbore in FP32 (two-sided, inclusive edges, 0 < t <= t_max); the
  * closest hit per ray is the smallest (t, triangle id).  The (t, u, v) of the
- * winning triangle are then recomputed in FP64 from the FP32 inputs and
- * rounded to FP32.  Hits are written at each ray's ray_id.  Counters final_*
+ * winning triangle are then recomputed in double-word (float + float, about
+ * 48-bit) arithmetic from the FP32 inputs and rounded to FP32.  Hits are written at each ray's ray_id.  Counters final_*
  * reset and written by this call.  Workspace: crsh_closest_hit_workspace. */
 crsh_status crsh_closest_hit(const crsh_hierarchy *h, const crsh_rays *rays, const uint32_t *n_rays,
                              const crsh_scene *scene, const crsh_pairs *pairs, crsh_hits *out,

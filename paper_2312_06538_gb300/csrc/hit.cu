@@ -13,7 +13,8 @@
 // the result does not depend on scheduling.  A last pass recomputes (t, u, v)
 // of the winning triangle with the same test and scatters hits to the rays'
 // generation order.  Decisions (which triangle is closest) are FP32; the
-// reported (t, u, v) of the winner are recomputed in FP64 from the FP32 inputs.
+// reported (t, u, v) of the winner are recomputed in double-word (float +
+// float) arithmetic from the FP32 inputs.
 #include <atomic>
 #include <mutex>
 
@@ -70,12 +71,31 @@ __device__ __forceinline__ unsigned long long hit_key(float t, unsigned tri) {
 // kid2 = (1 + K) / |d|^2; a zero direction makes s = 0 and 0 x inf a NaN, so
 // the test rejects, as Moller-Trumbore would (its determinant is 0).
 constexpr float PRETEST_K1 = 1.000002f;
+// Operation order written out: the packed twin below computes each of its
+// two lanes with exactly these FP32 operations, so both give the same bits.
 __device__ __forceinline__ bool near_line(float ox, float oy, float oz, float dx, float dy, float dz, float kid2,
                                           float4 C) {
-    const float vx = C.x - ox, vy = C.y - oy, vz = C.z - oz;
-    const float vv = vx * vx + vy * vy + vz * vz;
-    const float s = vx * dx + vy * dy + vz * dz;
-    return vv <= fmaf(s * s, kid2, C.w);
+    const float vx = __fadd_rn(C.x, -ox), vy = __fadd_rn(C.y, -oy), vz = __fadd_rn(C.z, -oz);
+    const float vv = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+    const float s = __fmaf_rn(vz, dz, __fmaf_rn(vy, dy, __fmul_rn(vx, dx)));
+    return vv <= __fmaf_rn(__fmul_rn(s, s), kid2, C.w);
+}
+
+// The same pre-test for two rays at once (Blackwell's paired FP32 operations,
+// one instruction for both lanes of a float2): rays in the .x and .y lanes of
+// (-o, d, kid2), the triangle's centre and q repeated in both lanes.
+struct RayPair {
+    float2 nox, noy, noz, dx, dy, dz, kid2;
+};
+__device__ __forceinline__ void near_line2(const RayPair& p, float4 cxy, float4 czq, bool& h0, bool& h1) {
+    const float2 vx = __fadd2_rn(make_float2(cxy.x, cxy.y), p.nox);
+    const float2 vy = __fadd2_rn(make_float2(cxy.z, cxy.w), p.noy);
+    const float2 vz = __fadd2_rn(make_float2(czq.x, czq.y), p.noz);
+    const float2 vv = __ffma2_rn(vz, vz, __ffma2_rn(vy, vy, __fmul2_rn(vx, vx)));
+    const float2 sd = __ffma2_rn(vz, p.dz, __ffma2_rn(vy, p.dy, __fmul2_rn(vx, p.dx)));
+    const float2 rhs = __ffma2_rn(__fmul2_rn(sd, sd), p.kid2, make_float2(czq.z, czq.w));
+    h0 = vv.x <= rhs.x;
+    h1 = vv.y <= rhs.y;
 }
 
 constexpr unsigned long long NO_HIT = ~0ull;
@@ -86,6 +106,22 @@ struct RaysDev {
 };
 
 constexpr int CH_WARPS = 4, CH_BLOCK = CH_WARPS * 32;
+
+// kid2 of a ray, with its operation order written out (every kernel that
+// pre-tests a ray computes the same bits)
+__device__ __forceinline__ float ray_kid2(float dx, float dy, float dz) {
+    return __fdiv_rn(PRETEST_K1, __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+__device__ __forceinline__ void prefetch_node_rays(const RaysDev& rays, unsigned i) {
+    prefetch_l1(rays.ox + i); prefetch_l1(rays.oy + i); prefetch_l1(rays.oz + i);
+    prefetch_l1(rays.dx + i); prefetch_l1(rays.dy + i); prefetch_l1(rays.dz + i);
+    prefetch_l1(rays.tmax + i);
+}
+
+constexpr unsigned CH_PAIRS = 128;   // pairs per work chunk
 
 // min over the lanes that hold the same ray (one per stream), then one
 // atomicMin per ray
@@ -100,40 +136,29 @@ __device__ __forceinline__ void flush_best(unsigned long long bk, bool rvalid, i
     if (rvalid && sidx == 0 && bk != NO_HIT) atomicMin(&best[ray], bk);
 }
 
-struct Ray7 {
-    float ox, oy, oz, dx, dy, dz, tmax, id2;
-};
-
-__device__ __forceinline__ Ray7 load_ray(const RaysDev& rays, unsigned i) {
-    Ray7 r{rays.ox[i], rays.oy[i], rays.oz[i], rays.dx[i], rays.dy[i], rays.dz[i], rays.tmax[i], 0.f};
-    r.id2 = PRETEST_K1 / (r.dx * r.dx + r.dy * r.dy + r.dz * r.dz);
-    return r;
-}
-
-
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-
-constexpr unsigned CH_PAIRS = 128;   // pairs per work chunk
-
 // Warps take chunks of CH_PAIRS consecutive pairs of the node-sorted pair
 // list from an atomic counter (the cost of a chunk depends on how many nodes
 // it spans) and walk them in groups: up to 32 consecutive pairs of one node.
-// Each lane holds two rays of the node (slots r and r + B/2); the 32 / (B/2)
-// streams of the warp walk every S-th triangle of the group, so each triangle
-// record read from shared memory serves two tests.  Software pipeline: while
-// group g is tested, the records of group g+1 are copied into the other
-// shared buffer (cp.async), the pair window of group g+2 is loaded into
-// registers and the chunk after the current one is already claimed, so the
-// chain counter -> pair -> triangle -> record never stalls the tests.
-// *work must be 0 at launch.
+// Each lane holds two rays of the node (slots r and r + B/2) as a RayPair;
+// the 32 / (B/2) streams of the warp walk every S-th triangle of the group and
+// pre-test it against both rays with one set of paired FP32 operations, then
+// run Moller-Trumbore on the survivors.  Software pipeline: while group g is
+// tested, the records of group g+1 are copied into the other shared buffer
+// (cp.async), the pair window of group g+2 is loaded into registers and the
+// chunk after the current one is already claimed, so the chain counter ->
+// pair -> triangle -> record never stalls the tests.  *work must be 0 at
+// launch.
 template <int B>
-__global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, const uint32_t* ptri,
-                                                      const unsigned* p_count, unsigned long long p_cap,
-                                                      RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
-                                                      unsigned long long* best, unsigned* work, crsh_counters* ctr) {
+__global__ void __launch_bounds__(CH_BLOCK, 6) k_closest(const uint32_t* pnode, const uint32_t* ptri,
+                                                         const unsigned* p_count, unsigned long long p_cap,
+                                                         RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
+                                                         unsigned long long* best, unsigned* work,
+                                                         crsh_counters* ctr) {
     constexpr int H = B / 2;            // lanes per node (two rays each)
     constexpr int S = 32 / H;           // streams
-    __shared__ __align__(16) float4 s_tri[CH_WARPS][2][32][4];
+    // one 64-byte record per triangle: a lane's four copies land side by side
+    // (a component-major layout measured 25 % slower on the copies)
+    __shared__ __align__(16) float4 s_tri[CH_WARPS][2][32][4];    // (a, n.x) (e1, n.y) (e2, n.z) (c, q)
     __shared__ unsigned s_tid[CH_WARPS][2][32];
     const unsigned P = (unsigned)min((unsigned long long)*p_count, p_cap);
     const unsigned N = *n_ptr;
@@ -176,19 +201,42 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
             }
             cp_async_commit();
         };
+        // the node's two rays of this lane (a missing ray gets kid2 = NaN:
+        // its pre-tests all fail)
+        RayPair rp;
+        float ta = 0.f, tb = 0.f;
+        unsigned cur, ray0, ray1;
+        bool v0, v1;
+        auto enter_node = [&](unsigned node) {
+            cur = node;
+            ray0 = cur * B + r;
+            ray1 = ray0 + H;
+            v0 = ray0 < N;
+            v1 = ray1 < N;
+            float ax = 0, ay = 0, az = 0, adx = 0, ady = 0, adz = 0;
+            float bx = 0, by = 0, bz = 0, bdx = 0, bdy = 0, bdz = 0;
+            ta = tb = 0.f;
+            if (v0) {
+                ax = rays.ox[ray0]; ay = rays.oy[ray0]; az = rays.oz[ray0];
+                adx = rays.dx[ray0]; ady = rays.dy[ray0]; adz = rays.dz[ray0]; ta = rays.tmax[ray0];
+            }
+            if (v1) {
+                bx = rays.ox[ray1]; by = rays.oy[ray1]; bz = rays.oz[ray1];
+                bdx = rays.dx[ray1]; bdy = rays.dy[ray1]; bdz = rays.dz[ray1]; tb = rays.tmax[ray1];
+            }
+            rp.nox = make_float2(-ax, -bx); rp.noy = make_float2(-ay, -by); rp.noz = make_float2(-az, -bz);
+            rp.dx = make_float2(adx, bdx); rp.dy = make_float2(ady, bdy); rp.dz = make_float2(adz, bdz);
+            rp.kid2 = make_float2(v0 ? ray_kid2(adx, ady, adz) : __int_as_float(0x7fc00000),
+                                  v1 ? ray_kid2(bdx, bdy, bdz) : __int_as_float(0x7fc00000));
+        };
         unsigned q1 = c_first * CH_PAIRS, e1 = min(P, q1 + CH_PAIRS);
         unsigned pw1, pt1;
         window(q1, e1, pw1, pt1);
-        unsigned cur = __shfl_sync(FULL, pw1, 0);
+        enter_node(__shfl_sync(FULL, pw1, 0));
         unsigned cnt = __popc(__ballot_sync(FULL, pw1 == cur));   // a prefix: pairs are node-sorted
         stage(0, cnt, pt1);
         bool has1 = advance(q1, e1, cnt);
         if (has1) window(q1, e1, pw1, pt1);
-        unsigned ray0 = cur * B + r, ray1 = ray0 + H;
-        bool v0 = ray0 < N, v1 = ray1 < N;
-        Ray7 a{0, 0, 0, 0, 0, 0, 0, 0}, b{0, 0, 0, 0, 0, 0, 0, 0};
-        if (v0) a = load_ray(rays, ray0);
-        if (v1) b = load_ray(rays, ray1);
         unsigned long long k0 = NO_HIT, k1 = NO_HIT;
         int buf = 0;
         for (;;) {
@@ -203,11 +251,7 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
                 if (has2) window(q1, e1, pw2, pt2);
                 if (nnode != cur) {   // warm L1 with the next node's rays
                     const unsigned nr = nnode * B + r;
-                    if (nr < N) {
-                        prefetch_l1(rays.ox + nr); prefetch_l1(rays.oy + nr); prefetch_l1(rays.oz + nr);
-                        prefetch_l1(rays.dx + nr); prefetch_l1(rays.dy + nr); prefetch_l1(rays.dz + nr);
-                        prefetch_l1(rays.tmax + nr);
-                    }
+                    if (nr < N) prefetch_node_rays(rays, nr);
                 }
             } else {
                 cp_async_commit();   // keeps "all but the newest group" meaning this group
@@ -216,34 +260,38 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
             __syncwarp();
             const unsigned nrays = min((unsigned)B, N - cur * B);
             if (lane == 0) n_tests += (unsigned long long)cnt * nrays;
-            if (v0) {
-                // pre-test every (ray, triangle) of the lane; bit k = triangle sidx + S k
-                unsigned m0 = 0, m1 = 0;
-                unsigned k = 0;
-                for (unsigned j = sidx; j < cnt; j += S, ++k) {
-                    const float4 C = s_tri[warp][buf][j][3];
-                    m0 |= (unsigned)near_line(a.ox, a.oy, a.oz, a.dx, a.dy, a.dz, a.id2, C) << k;
-                    m1 |= (unsigned)(v1 && near_line(b.ox, b.oy, b.oz, b.dx, b.dy, b.dz, b.id2, C)) << k;
+            // pre-test every (ray, triangle) of the lane; bit k = triangle sidx + S k
+            unsigned m0 = 0, m1 = 0;
+#pragma unroll
+            for (int k = 0; k < 32 / S; ++k) {
+                const unsigned j = sidx + S * k;
+                if (j < cnt) {
+                    bool h0, h1;
+                    const float4 c = s_tri[warp][buf][j][3];
+                    near_line2(rp, make_float4(c.x, c.x, c.y, c.y), make_float4(c.z, c.z, c.w, c.w), h0, h1);
+                    m0 |= (unsigned)h0 << k;
+                    m1 |= (unsigned)h1 << k;
                 }
-                // Moller-Trumbore on the survivors
-                unsigned m = m0 | m1;
-                while (m) {
-                    const unsigned kk = __ffs(m) - 1;
-                    m &= m - 1;
-                    const unsigned j = sidx + S * kk;
-                    const float4 A = s_tri[warp][buf][j][0], E1 = s_tri[warp][buf][j][1],
-                                 E2 = s_tri[warp][buf][j][2];
-                    float t;
-                    if (((m0 >> kk) & 1u) && mt_hit(a.ox, a.oy, a.oz, a.dx, a.dy, a.dz, a.tmax, A, E1, E2, t)) {
-                        ++n_hits;
-                        const unsigned long long key = hit_key(t, s_tid[warp][buf][j]);
-                        k0 = key < k0 ? key : k0;
-                    }
-                    if (((m1 >> kk) & 1u) && mt_hit(b.ox, b.oy, b.oz, b.dx, b.dy, b.dz, b.tmax, A, E1, E2, t)) {
-                        ++n_hits;
-                        const unsigned long long key = hit_key(t, s_tid[warp][buf][j]);
-                        k1 = key < k1 ? key : k1;
-                    }
+            }
+            // Moller-Trumbore on the survivors (o = -(-o) is exact)
+            unsigned m = m0 | m1;
+            while (m) {
+                const unsigned kk = __ffs(m) - 1;
+                m &= m - 1;
+                const unsigned j = sidx + S * kk;
+                const float4 A = s_tri[warp][buf][j][0], E1 = s_tri[warp][buf][j][1], E2 = s_tri[warp][buf][j][2];
+                float t;
+                if (((m0 >> kk) & 1u) &&
+                    mt_hit(-rp.nox.x, -rp.noy.x, -rp.noz.x, rp.dx.x, rp.dy.x, rp.dz.x, ta, A, E1, E2, t)) {
+                    ++n_hits;
+                    const unsigned long long key = hit_key(t, s_tid[warp][buf][j]);
+                    k0 = key < k0 ? key : k0;
+                }
+                if (((m1 >> kk) & 1u) &&
+                    mt_hit(-rp.nox.y, -rp.noy.y, -rp.noz.y, rp.dx.y, rp.dy.y, rp.dz.y, tb, A, E1, E2, t)) {
+                    ++n_hits;
+                    const unsigned long long key = hit_key(t, s_tid[warp][buf][j]);
+                    k1 = key < k1 ? key : k1;
                 }
             }
             __syncwarp();   // buffer buf is refilled two groups on
@@ -251,24 +299,14 @@ __global__ void __launch_bounds__(CH_BLOCK) k_closest(const uint32_t* pnode, con
                 const unsigned prev = __shfl_up_sync(FULL, pw2, 1);
                 if (pw2 != 0xffffffffu && (lane == 0 || prev != pw2)) {
                     const unsigned nr = pw2 * B;   // the node's B rays share one 64-byte-aligned span per array
-                    if (nr < N) {
-                        prefetch_l1(rays.ox + nr); prefetch_l1(rays.oy + nr); prefetch_l1(rays.oz + nr);
-                        prefetch_l1(rays.dx + nr); prefetch_l1(rays.dy + nr); prefetch_l1(rays.dz + nr);
-                        prefetch_l1(rays.tmax + nr);
-                    }
+                    if (nr < N) prefetch_node_rays(rays, nr);
                 }
             }
             if (!has1) break;
             if (nnode != cur) {
                 flush_best<H>(k0, v0, sidx, ray0, best);
                 flush_best<H>(k1, v1, sidx, ray1, best);
-                cur = nnode;
-                ray0 = cur * B + r;
-                ray1 = ray0 + H;
-                v0 = ray0 < N;
-                v1 = ray1 < N;
-                if (v0) a = load_ray(rays, ray0);
-                if (v1) b = load_ray(rays, ray1);
+                enter_node(nnode);
                 k0 = k1 = NO_HIT;
             }
             cnt = ncnt;
@@ -295,26 +333,82 @@ __global__ void k_fill_best(unsigned long long* best, const unsigned* n_ptr, uns
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) best[i] = NO_HIT;
 }
 
-// Moller-Trumbore in FP64 on the FP32 inputs, for the one winning triangle
-// of a ray: the FP32 test decides which triangle is closest, this pass
-// reports its (t, u, v) to FP32 rounding (FP32 alone loses digits in
-// proportion to distance / triangle size).
-__device__ __forceinline__ void mt_refine(double ox, double oy, double oz, double dx, double dy, double dz,
-                                          const crsh_scene& sc, unsigned tri, float& t, float& u, float& v) {
-    const double ax = sc.v0x[tri], ay = sc.v0y[tri], az = sc.v0z[tri];
-    const double e1x = (double)sc.v1x[tri] - ax, e1y = (double)sc.v1y[tri] - ay, e1z = (double)sc.v1z[tri] - az;
-    const double e2x = (double)sc.v2x[tri] - ax, e2y = (double)sc.v2y[tri] - ay, e2z = (double)sc.v2z[tri] - az;
-    const double px = dy * e2z - dz * e2y, py = dz * e2x - dx * e2z, pz = dx * e2y - dy * e2x;
-    const double det = e1x * px + e1y * py + e1z * pz;
-    const double inv = 1.0 / det;
-    const double sx = ox - ax, sy = oy - ay, sz = oz - az;
-    const double qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
-    u = (float)((sx * px + sy * py + sz * pz) * inv);
-    v = (float)((dx * qx + dy * qy + dz * qz) * inv);
-    t = (float)((e2x * qx + e2y * qy + e2z * qz) * inv);
+// ---- double-word (float + float) arithmetic --------------------------------
+// A value is the unevaluated sum h + l of two FP32 numbers (about 48 bits).
+// Error-free transformations: TwoSum (Knuth), FastTwoSum (Dekker, |a| >= |b|),
+// TwoProd with an FMA; sums and products of double-words follow Joldes,
+// Muller and Popescu, "Tight and rigorous error bounds for basic building
+// blocks of double-word arithmetic" (ACM TOMS 2017): the accurate sum
+// (relative error <= 3u^2 + 13u^3) and the FMA product (<= 5u^2), u = 2^-24.
+// Every step is an explicit _rn intrinsic, so nothing is contracted or
+// reassociated.
+struct DW {
+    float h, l;
+};
+__device__ __forceinline__ DW two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DW fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DW dw_add(DW x, DW y) {
+    const DW s = two_sum(x.h, y.h), t = two_sum(x.l, y.l);
+    const DW v = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+    return fast_two_sum(v.h, __fadd_rn(t.l, v.l));
+}
+__device__ __forceinline__ DW dw_neg(DW x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ DW dw_mul(DW x, DW y) {
+    const float ch = __fmul_rn(x.h, y.h);
+    const float cl1 = __fmaf_rn(x.h, y.h, -ch);
+    const float cl2 = __fmaf_rn(x.l, y.h, __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.l)));
+    return fast_two_sum(ch, __fadd_rn(cl1, cl2));
+}
+// a (one FP32 number) times a double-word
+__device__ __forceinline__ DW dw_mul(float a, DW y) {
+    const float ch = __fmul_rn(a, y.h);
+    const float cl = __fmaf_rn(a, y.l, __fmaf_rn(a, y.h, -ch));
+    return fast_two_sum(ch, cl);
+}
+// x / y rounded to FP32: an FP32 quotient corrected by the double-word
+// remainder x - q y (the product q y.h is exact as a TwoProd)
+__device__ __forceinline__ float dw_div_f(DW x, DW y) {
+    const float q = __fdiv_rn(x.h, y.h);
+    const float ph = __fmul_rn(q, y.h);
+    const float pl = __fmaf_rn(q, y.h, -ph);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.h, ph), pl), __fmaf_rn(-q, y.l, x.l));
+    return __fadd_rn(q, __fdiv_rn(r, y.h));
 }
 
-// winner's (t, u, v) from the FP64 refinement; scatter to ray_id order
+// Moller-Trumbore in double-word arithmetic on the FP32 inputs, for the one
+// winning triangle of a ray: the FP32 test decides which triangle is closest,
+// this pass reports its (t, u, v) to about FP32 rounding (FP32 alone loses
+// digits in proportion to distance / triangle size).  Differences of the
+// FP32 inputs are exact double-words; the rest carries about 2^-44 relative
+// error, far below the FP32 rounding of the results.
+__device__ __forceinline__ void mt_refine(float ox, float oy, float oz, float dx, float dy, float dz,
+                                          const crsh_scene& sc, unsigned tri, float& t, float& u, float& v) {
+    const float ax = sc.v0x[tri], ay = sc.v0y[tri], az = sc.v0z[tri];
+    const DW e1x = two_sum(sc.v1x[tri], -ax), e1y = two_sum(sc.v1y[tri], -ay), e1z = two_sum(sc.v1z[tri], -az);
+    const DW e2x = two_sum(sc.v2x[tri], -ax), e2y = two_sum(sc.v2y[tri], -ay), e2z = two_sum(sc.v2z[tri], -az);
+    // p = d x e2
+    const DW px = dw_add(dw_mul(dy, e2z), dw_neg(dw_mul(dz, e2y)));
+    const DW py = dw_add(dw_mul(dz, e2x), dw_neg(dw_mul(dx, e2z)));
+    const DW pz = dw_add(dw_mul(dx, e2y), dw_neg(dw_mul(dy, e2x)));
+    const DW det = dw_add(dw_add(dw_mul(e1x, px), dw_mul(e1y, py)), dw_mul(e1z, pz));
+    const DW sx = two_sum(ox, -ax), sy = two_sum(oy, -ay), sz = two_sum(oz, -az);
+    // q = s x e1
+    const DW qx = dw_add(dw_mul(sy, e1z), dw_neg(dw_mul(sz, e1y)));
+    const DW qy = dw_add(dw_mul(sz, e1x), dw_neg(dw_mul(sx, e1z)));
+    const DW qz = dw_add(dw_mul(sx, e1y), dw_neg(dw_mul(sy, e1x)));
+    u = dw_div_f(dw_add(dw_add(dw_mul(sx, px), dw_mul(sy, py)), dw_mul(sz, pz)), det);
+    v = dw_div_f(dw_add(dw_add(dw_mul(dx, qx), dw_mul(dy, qy)), dw_mul(dz, qz)), det);
+    t = dw_div_f(dw_add(dw_add(dw_mul(e2x, qx), dw_mul(e2y, qy)), dw_mul(e2z, qz)), det);
+}
+
+// winner's (t, u, v) from the double-word refinement; scatter to ray_id order
 __global__ void k_finalize(RaysDev rays, const unsigned* n_ptr, crsh_scene sc, const unsigned long long* best,
                            crsh_hits out) {
     const unsigned n = *n_ptr;
@@ -351,7 +445,7 @@ __global__ void __launch_bounds__(BF_BLOCK) k_brute(RaysDev rays, const unsigned
             dx = rays.dx[i]; dy = rays.dy[i]; dz = rays.dz[i];
             tmax = rays.tmax[i];
         }
-        const float id2 = PRETEST_K1 / (dx * dx + dy * dy + dz * dz);
+        const float id2 = ray_kid2(dx, dy, dz);
         unsigned long long bk = NO_HIT;
         for (unsigned t0 = 0; t0 < n_tris; t0 += BF_BLOCK) {
             __syncthreads();
