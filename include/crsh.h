@@ -19,7 +19,9 @@
  *    otherwise; the structs themselves live in host memory and are read during
  *    the call only.
  *  - The caller owns every buffer (inputs, outputs, workspaces).  The library
- *    allocates no device memory.
+ *    allocates no device memory.  A workspace pointer must be 256-byte
+ *    aligned (cudaMalloc's and PyTorch's allocations are); another one is an
+ *    argument error.
  *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy
  *    default stream).  Data-dependent sizes (ray count, pair counts) stay on
  *    the device; no call synchronises with the host, so the sequence can be

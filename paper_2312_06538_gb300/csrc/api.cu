@@ -143,12 +143,16 @@ size_t crsh_hash_sort_workspace(uint32_t capacity, uint32_t max_pixels) {
     return hash_sort_workspace(capacity, max_pixels);
 }
 
+// Workspaces are carved into 256-byte-aligned arrays that kernels read with
+// 16-byte vector accesses, so the base must be 256-byte aligned.
+static bool ws_ok(const void* w) { return w != nullptr && (reinterpret_cast<uintptr_t>(w) & 255u) == 0; }
+
 crsh_status crsh_hash_sort(const crsh_gbuffer* gbuffer, const crsh_rays_in* rays_in, const float* lights,
                            uint32_t n_lights, const crsh_hash_params* p, crsh_rays* out, uint32_t* keys_out,
                            uint32_t* n_out, crsh_counters* counters, void* workspace, size_t workspace_bytes,
                            void* stream) {
     if ((gbuffer == nullptr) == (rays_in == nullptr)) return CRSH_ERR_INVALID_ARG;
-    if (!p || !rays_ok(out) || !keys_out || !n_out || !counters || !workspace) return CRSH_ERR_INVALID_ARG;
+    if (!p || !rays_ok(out) || !keys_out || !n_out || !counters || !ws_ok(workspace)) return CRSH_ERR_INVALID_ARG;
     if (p->shadow_theta_bits < 1 || p->shadow_theta_bits > 13 || p->shadow_phi_bits < 3 || p->shadow_phi_bits > 13 ||
         p->shadow_theta_bits + p->shadow_phi_bits > 30)
         return CRSH_ERR_INVALID_ARG;
@@ -200,7 +204,7 @@ size_t crsh_traverse_workspace(const crsh_hierarchy* h, uint32_t n_tris, uint32_
 crsh_status crsh_traverse(const crsh_hierarchy* h, const crsh_scene* scene, const crsh_traverse_params* p,
                           crsh_pairs* out, crsh_counters* counters, void* workspace, size_t workspace_bytes,
                           void* stream) {
-    if (!hier_ok(h) || !scene_ok(scene, true) || !p || !out || !counters || !workspace) return CRSH_ERR_INVALID_ARG;
+    if (!hier_ok(h) || !scene_ok(scene, true) || !p || !out || !counters || !ws_ok(workspace)) return CRSH_ERR_INVALID_ARG;
     if (!out->node || !out->tri || !out->node_offsets || !out->count || out->capacity == 0 ||
         out->capacity > (1ull << 31))
         return CRSH_ERR_INVALID_ARG;
@@ -216,7 +220,7 @@ crsh_status crsh_closest_hit(const crsh_hierarchy* h, const crsh_rays* rays, con
                              const crsh_scene* scene, const crsh_pairs* pairs, crsh_hits* out,
                              crsh_counters* counters, void* workspace, size_t workspace_bytes, void* stream) {
     if (!hier_ok(h) || !rays_ok(rays) || !n_rays || !scene_ok(scene, true) || !pairs || !pairs->node ||
-        !pairs->tri || !pairs->count || !out || !out->tri || !out->t || !out->u || !out->v || !counters || !workspace)
+        !pairs->tri || !pairs->count || !out || !out->tri || !out->t || !out->u || !out->v || !counters || !ws_ok(workspace))
         return CRSH_ERR_INVALID_ARG;
     DeviceInfo dev;
     if (!current_device(dev)) return CRSH_ERR_CUDA;
@@ -244,7 +248,7 @@ crsh_status crsh_closest_hit_backward(const crsh_rays* rays, const uint32_t* n_r
                                       float* g_verts, float* g_orig, float* g_dir, crsh_counters* counters,
                                       void* workspace, size_t workspace_bytes, void* stream) {
     if (!rays_ok(rays) || !n_rays || !scene_ok(scene, false) || !hits || !hits->tri || !hits->t || !hits->u ||
-        !hits->v || !g_t || !g_u || !g_v || !g_verts || !g_orig || !g_dir || !workspace)
+        !hits->v || !g_t || !g_u || !g_v || !g_verts || !g_orig || !g_dir || !ws_ok(workspace))
         return CRSH_ERR_INVALID_ARG;
     DeviceInfo dev;
     if (!current_device(dev)) return CRSH_ERR_CUDA;
@@ -255,7 +259,7 @@ crsh_status crsh_closest_hit_backward(const crsh_rays* rays, const uint32_t* n_r
 crsh_status crsh_bruteforce_closest_hit(const crsh_rays* rays, const uint32_t* n_rays, const crsh_scene* scene,
                                         crsh_hits* out, void* workspace, size_t workspace_bytes, void* stream) {
     if (!rays_ok(rays) || !n_rays || !scene_ok(scene, true) || !out || !out->tri || !out->t || !out->u || !out->v ||
-        !workspace)
+        !ws_ok(workspace))
         return CRSH_ERR_INVALID_ARG;
     DeviceInfo dev;
     if (!current_device(dev)) return CRSH_ERR_CUDA;

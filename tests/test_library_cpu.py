@@ -91,6 +91,20 @@ def test_argument_errors_are_synchronous():
                                 0, None) == C.ERR_INVALID_ARG
 
 
+def test_misaligned_workspace_is_an_argument_error():
+    """Workspaces are carved into 256-byte-aligned arrays read with 16-byte
+    vector accesses; a base off that alignment is refused before any launch
+    (only the refused case is called: the pointers here are not memory)."""
+    lib = C.load()
+    P = ctypes.c_void_p
+    hp = C.crsh_hash_params((C.F32 * 3)(0, 0, 0), (C.F32 * 3)(1, 1, 1), 13, 13, 5, 7, 8, 1, 1, 1)
+    g = C.crsh_gbuffer(*([P(0x1000)] * 11), 16)
+    rays = C.crsh_rays(*([P(0x1000)] * 10), 64)
+    for off in (16, 128, 255):
+        assert lib.crsh_hash_sort(ctypes.byref(g), None, None, 0, ctypes.byref(hp), ctypes.byref(rays), P(0x1000),
+                                  P(0x1000), P(0x1000), P(0x10000 + off), 1 << 20, None) == C.ERR_INVALID_ARG
+
+
 def test_workspace_queries_are_monotone():
     assert C.crsh_hash_sort_workspace(1000, 100) < C.crsh_hash_sort_workspace(100000, 100)
     assert C.crsh_closest_hit_workspace(10) < C.crsh_closest_hit_workspace(1000)
