@@ -182,14 +182,15 @@ template <int B>
 __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned L, Pads pads,
                                                  LevelOut out, unsigned* counts, Caps caps) {
     constexpr unsigned S = B + 1, W = 32 * S;
-    extern __shared__ float s_rows[];   // 7 x W floats: ox oy oz dx dy dz r
-    float* sox = s_rows;
-    float* soy = s_rows + W;
-    float* soz = s_rows + 2 * W;
-    float* sdx = s_rows + 3 * W;
-    float* sdy = s_rows + 4 * W;
-    float* sdz = s_rows + 5 * W;
-    float* srad = s_rows + 6 * W;
+    // 4 x W floats: three staged components (directions for the cone, then
+    // origins for the sphere) and the sphere radii; staging the two halves in
+    // turn halves the shared memory of a warp, so twice as many warps are
+    // resident to hide the loads and the FP32 dependency chains
+    extern __shared__ float s_rows[];
+    float* s0 = s_rows;
+    float* s1 = s_rows + W;
+    float* s2 = s_rows + 2 * W;
+    float* srad = s_rows + 3 * W;
     const unsigned n = *n_ptr;
     const unsigned cnt = (n + B - 1) / B;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
     }
     const unsigned lim = min(cnt, out.cap);
     const unsigned lane = threadIdx.x;
-    for (unsigned j0 = blockIdx.x * 32; j0 < lim; j0 += gridDim.x * 32) {
+    // the 32 nodes' rays of three arrays into s0..s2 (coalesced: lane = ray)
+    auto stage = [&](unsigned j0, const float* ax, const float* ay, const float* az) {
 #pragma unroll
         for (unsigned t = 0; t < B; ++t) {
             const unsigned idx = t * 32 + lane;          // ray within this block of 32 nodes
@@ -214,41 +216,45 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
             const size_t i = (size_t)j0 * B + idx;       // sorted ray
             if (j0 + k < lim && i < n) {
                 const unsigned a = k * S + r;
-                sox[a] = rays.ox[i];
-                soy[a] = rays.oy[i];
-                soz[a] = rays.oz[i];
-                sdx[a] = rays.dx[i];
-                sdy[a] = rays.dy[i];
-                sdz[a] = rays.dz[i];
+                s0[a] = ax[i];
+                s1[a] = ay[i];
+                s2[a] = az[i];
             }
         }
         __syncwarp();
+    };
+    for (unsigned j0 = blockIdx.x * 32; j0 < lim; j0 += gridDim.x * 32) {
         const unsigned j = j0 + lane;
-        if (j < lim) {
-            const unsigned m = min((unsigned)B, n - j * B);
-            const unsigned b = lane * S;
-            // sphere: radius-0 leaves, balanced pairwise tree in ray order (eqs. 7-8)
+        const unsigned m = j < lim ? min((unsigned)B, n - j * B) : 0u;
+        const unsigned b = lane * S;
+        // cone: the rays in sorted order (eqs. 1-4)
+        stage(j0, rays.dx, rays.dy, rays.dz);
+        ConeFold f;
+        if (m) {
+            f.start(unit(mk3(s0[b], s1[b], s2[b])));
+            for (unsigned i = 1; i < m; ++i) f.add(unit(mk3(s0[b + i], s1[b + i], s2[b + i])));
+        }
+        __syncwarp();
+        // sphere: radius-0 leaves, balanced pairwise tree in ray order (eqs. 7-8)
+        stage(j0, rays.ox, rays.oy, rays.oz);
+        if (m) {
             for (unsigned i = 0; i < m; ++i) srad[b + i] = 0.0f;
             for (unsigned st = 1; st < m; st <<= 1) {
                 for (unsigned i = 0; i + st < m; i += 2 * st) {
                     SC x, y;
-                    x.c = mk3(sox[b + i], soy[b + i], soz[b + i]);
+                    x.c = mk3(s0[b + i], s1[b + i], s2[b + i]);
                     x.r = srad[b + i];
-                    y.c = mk3(sox[b + i + st], soy[b + i + st], soz[b + i + st]);
+                    y.c = mk3(s0[b + i + st], s1[b + i + st], s2[b + i + st]);
                     y.r = srad[b + i + st];
                     sphere_union(x, y);
-                    sox[b + i] = x.c.x;
-                    soy[b + i] = x.c.y;
-                    soz[b + i] = x.c.z;
+                    s0[b + i] = x.c.x;
+                    s1[b + i] = x.c.y;
+                    s2[b + i] = x.c.z;
                     srad[b + i] = x.r;
                 }
             }
-            // cone: the rays in sorted order (eqs. 1-4)
-            ConeFold f;
-            f.start(unit(mk3(sdx[b], sdy[b], sdz[b])));
-            for (unsigned i = 1; i < m; ++i) f.add(unit(mk3(sdx[b + i], sdy[b + i], sdz[b + i])));
             SC node;
-            node.c = mk3(sox[b], soy[b], soz[b]);
+            node.c = mk3(s0[b], s1[b], s2[b]);
             node.r = srad[b];
             node.x = f.x;
             node.phi = f.phi();
@@ -263,7 +269,7 @@ template <int B>
 static void launch_build_l1(const RaysIn& ri, const uint32_t* n_rays, unsigned L, const Pads& pads,
                             const LevelOut& o1, unsigned* counts, const Caps& caps, unsigned cap0, cudaStream_t s,
                             const DeviceInfo& dev) {
-    const size_t smem = 7 * 32 * (B + 1) * sizeof(float);
+    const size_t smem = 4 * 32 * (B + 1) * sizeof(float);
     const unsigned blocks = (cap0 + 31) / 32;
     const unsigned grid = blocks < (unsigned)dev.sms * 32 ? (blocks ? blocks : 1) : dev.sms * 32;
     k_build_l1<B><<<grid, 32, smem, s>>>(ri, n_rays, L, pads, o1, counts, caps);
