@@ -20,6 +20,8 @@ struct SC {
     float phi;
 };
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Square root and quotient to a few ulps (special-function unit); the
 // padding applied after each merge covers their error.
 __device__ __forceinline__ float sqrt_fast(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
@@ -223,10 +225,28 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
         }
         __syncwarp();
     };
+    // warm L2 with three arrays' spans of the block of 32 nodes at j0 (one
+    // 128-byte line per lane and array: 32 nodes x B rays x 4 bytes = B lines)
+    auto warm = [&](unsigned j0, const float* ax, const float* ay, const float* az) {
+        if (j0 >= lim) return;
+        const size_t i0 = (size_t)j0 * B;
+        for (unsigned l = lane; l < B; l += 32) {
+            const size_t i = i0 + 32 * l;
+            if (i < n) {
+                prefetch_l2(ax + i);
+                prefetch_l2(ay + i);
+                prefetch_l2(az + i);
+            }
+        }
+    };
     for (unsigned j0 = blockIdx.x * 32; j0 < lim; j0 += gridDim.x * 32) {
         const unsigned j = j0 + lane;
         const unsigned m = j < lim ? min((unsigned)B, n - j * B) : 0u;
         const unsigned b = lane * S;
+        // this block's origins and the next block's directions load into L2
+        // while the cone and the sphere of this block are built
+        warm(j0, rays.ox, rays.oy, rays.oz);
+        warm(j0 + gridDim.x * 32, rays.dx, rays.dy, rays.dz);
         // cone: the rays in sorted order (eqs. 1-4)
         stage(j0, rays.dx, rays.dy, rays.dz);
         ConeFold f;
