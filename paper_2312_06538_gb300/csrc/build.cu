@@ -209,18 +209,39 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
     }
     const unsigned lim = min(cnt, out.cap);
     const unsigned lane = threadIdx.x;
-    // the 32 nodes' rays of three arrays into s0..s2 (coalesced: lane = ray)
+    // 16-byte loads need every array 16-byte aligned (B >= 4 keeps a float4 in one node)
+    const bool vec = B >= 4 && ((reinterpret_cast<uintptr_t>(rays.ox) | reinterpret_cast<uintptr_t>(rays.oy) |
+                                 reinterpret_cast<uintptr_t>(rays.oz) | reinterpret_cast<uintptr_t>(rays.dx) |
+                                 reinterpret_cast<uintptr_t>(rays.dy) | reinterpret_cast<uintptr_t>(rays.dz)) &
+                                15u) == 0;
+    // the 32 nodes' rays of three arrays into s0..s2 (coalesced: lane = ray,
+    // or lane = 4 rays when the whole block exists)
     auto stage = [&](unsigned j0, const float* ax, const float* ay, const float* az) {
+        if (vec && j0 + 32 <= lim && (size_t)(j0 + 32) * B <= n) {
+            const float4* vx = reinterpret_cast<const float4*>(ax + (size_t)j0 * B);
+            const float4* vy = reinterpret_cast<const float4*>(ay + (size_t)j0 * B);
+            const float4* vz = reinterpret_cast<const float4*>(az + (size_t)j0 * B);
 #pragma unroll
-        for (unsigned t = 0; t < B; ++t) {
-            const unsigned idx = t * 32 + lane;          // ray within this block of 32 nodes
-            const unsigned k = idx / B, r = idx % B;
-            const size_t i = (size_t)j0 * B + idx;       // sorted ray
-            if (j0 + k < lim && i < n) {
-                const unsigned a = k * S + r;
-                s0[a] = ax[i];
-                s1[a] = ay[i];
-                s2[a] = az[i];
+            for (unsigned t = 0; t < B / 4; ++t) {
+                const unsigned q = t * 32 + lane;        // float4 within the block
+                const unsigned e = 4 * q, a = (e / B) * S + e % B;
+                const float4 X = vx[q], Y = vy[q], Z = vz[q];
+                s0[a] = X.x; s0[a + 1] = X.y; s0[a + 2] = X.z; s0[a + 3] = X.w;
+                s1[a] = Y.x; s1[a + 1] = Y.y; s1[a + 2] = Y.z; s1[a + 3] = Y.w;
+                s2[a] = Z.x; s2[a + 1] = Z.y; s2[a + 2] = Z.z; s2[a + 3] = Z.w;
+            }
+        } else {
+#pragma unroll
+            for (unsigned t = 0; t < B; ++t) {
+                const unsigned idx = t * 32 + lane;      // ray within this block of 32 nodes
+                const unsigned k = idx / B, r = idx % B;
+                const size_t i = (size_t)j0 * B + idx;   // sorted ray
+                if (j0 + k < lim && i < n) {
+                    const unsigned a = k * S + r;
+                    s0[a] = ax[i];
+                    s1[a] = ay[i];
+                    s2[a] = az[i];
+                }
             }
         }
         __syncwarp();
@@ -239,6 +260,7 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
             }
         }
     };
+    const bool unroll = lim >= 4u * 32u * gridDim.x;
     for (unsigned j0 = blockIdx.x * 32; j0 < lim; j0 += gridDim.x * 32) {
         const unsigned j = j0 + lane;
         const unsigned m = j < lim ? min((unsigned)B, n - j * B) : 0u;
@@ -249,30 +271,50 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
         warm(j0 + gridDim.x * 32, rays.dx, rays.dy, rays.dz);
         // cone: the rays in sorted order (eqs. 1-4)
         stage(j0, rays.dx, rays.dy, rays.dz);
+        // a full node (every node but perhaps the last) takes the unrolled
+        // loops: static shared-memory offsets, no loop or address arithmetic;
+        // only when each warp builds at least four blocks of nodes, so the
+        // longer code is fetched once for many nodes (on a 500 K-ray frame,
+        // one block per warp, the rolled loops measured faster)
         ConeFold f;
-        if (m) {
+        if (unroll && m == B) {
+            f.start(unit(mk3(s0[b], s1[b], s2[b])));
+#pragma unroll
+            for (unsigned i = 1; i < B; ++i) f.add(unit(mk3(s0[b + i], s1[b + i], s2[b + i])));
+        } else if (m) {
             f.start(unit(mk3(s0[b], s1[b], s2[b])));
             for (unsigned i = 1; i < m; ++i) f.add(unit(mk3(s0[b + i], s1[b + i], s2[b + i])));
         }
         __syncwarp();
         // sphere: radius-0 leaves, balanced pairwise tree in ray order (eqs. 7-8)
         stage(j0, rays.ox, rays.oy, rays.oz);
-        if (m) {
+        auto merge = [&](unsigned i, unsigned st) {
+            SC x, y;
+            x.c = mk3(s0[b + i], s1[b + i], s2[b + i]);
+            x.r = srad[b + i];
+            y.c = mk3(s0[b + i + st], s1[b + i + st], s2[b + i + st]);
+            y.r = srad[b + i + st];
+            sphere_union(x, y);
+            s0[b + i] = x.c.x;
+            s1[b + i] = x.c.y;
+            s2[b + i] = x.c.z;
+            srad[b + i] = x.r;
+        };
+        if (unroll && m == B) {
+#pragma unroll
+            for (unsigned i = 0; i < B; ++i) srad[b + i] = 0.0f;
+#pragma unroll
+            for (unsigned st = 1; st < B; st <<= 1) {
+#pragma unroll
+                for (unsigned i = 0; i + st < B; i += 2 * st) merge(i, st);
+            }
+        } else if (m) {
             for (unsigned i = 0; i < m; ++i) srad[b + i] = 0.0f;
             for (unsigned st = 1; st < m; st <<= 1) {
-                for (unsigned i = 0; i + st < m; i += 2 * st) {
-                    SC x, y;
-                    x.c = mk3(s0[b + i], s1[b + i], s2[b + i]);
-                    x.r = srad[b + i];
-                    y.c = mk3(s0[b + i + st], s1[b + i + st], s2[b + i + st]);
-                    y.r = srad[b + i + st];
-                    sphere_union(x, y);
-                    s0[b + i] = x.c.x;
-                    s1[b + i] = x.c.y;
-                    s2[b + i] = x.c.z;
-                    srad[b + i] = x.r;
-                }
+                for (unsigned i = 0; i + st < m; i += 2 * st) merge(i, st);
             }
+        }
+        if (m) {
             SC node;
             node.c = mk3(s0[b], s1[b], s2[b]);
             node.r = srad[b];
