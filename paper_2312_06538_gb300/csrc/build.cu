@@ -182,7 +182,7 @@ struct Caps {
 // stride puts the 32 lanes' reads in 32 distinct banks.
 template <int B>
 __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned L, Pads pads,
-                                                 LevelOut out, unsigned* counts, Caps caps) {
+                                                 LevelOut out, LevelOut out2, unsigned* counts, Caps caps) {
     constexpr unsigned S = B + 1, W = 32 * S;
     // 4 x W floats: three staged components (directions for the cone, then
     // origins for the sphere) and the sphere radii; staging the two halves in
@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
         }
     }
     const unsigned lim = min(cnt, out.cap);
+    const unsigned cnt2 = min((lim + B - 1) / B, caps.v[1]);   // level-2 nodes (when L >= 2)
     const unsigned lane = threadIdx.x;
     // 16-byte loads need every array 16-byte aligned (B >= 4 keeps a float4 in one node)
     const bool vec = B >= 4 && ((reinterpret_cast<uintptr_t>(rays.ox) | reinterpret_cast<uintptr_t>(rays.oy) |
@@ -314,8 +315,12 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
                 for (unsigned i = 0; i + st < m; i += 2 * st) merge(i, st);
             }
         }
+        SC node;
+        node.c = mk3(0.f, 0.f, 0.f);
+        node.r = 0.0f;
+        node.x = mk3(1.f, 0.f, 0.f);
+        node.phi = 0.0f;
         if (m) {
-            SC node;
             node.c = mk3(s0[b], s1[b], s2[b]);
             node.r = srad[b];
             node.x = f.x;
@@ -323,18 +328,30 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
             pad_node(node, pads);
             store_node(out, j, node);
         }
+        // level 2 (eqs. 5-8): the block's 32 nodes are 32 / B whole groups,
+        // merged here as the level-2 pass would merge them after reading the
+        // stored nodes back (the same values, in the same order)
+        if (L >= 2) {
+            const unsigned g = j / B, r2 = lane & (B - 1);
+            const unsigned m2 = g < cnt2 ? min((unsigned)B, lim - g * B) : 0u;
+            group_tree_merge<true>(node, r2, m2, B);
+            if (r2 == 0 && g < cnt2) {
+                pad_node(node, pads);
+                store_node(out2, g, node);
+            }
+        }
         __syncwarp();
     }
 }
 
 template <int B>
 static void launch_build_l1(const RaysIn& ri, const uint32_t* n_rays, unsigned L, const Pads& pads,
-                            const LevelOut& o1, unsigned* counts, const Caps& caps, unsigned cap0, cudaStream_t s,
-                            const DeviceInfo& dev) {
+                            const LevelOut& o1, const LevelOut& o2, unsigned* counts, const Caps& caps,
+                            unsigned cap0, cudaStream_t s, const DeviceInfo& dev) {
     const size_t smem = 4 * 32 * (B + 1) * sizeof(float);
     const unsigned blocks = (cap0 + 31) / 32;
     const unsigned grid = blocks < (unsigned)dev.sms * 32 ? (blocks ? blocks : 1) : dev.sms * 32;
-    k_build_l1<B><<<grid, 32, smem, s>>>(ri, n_rays, L, pads, o1, counts, caps);
+    k_build_l1<B><<<grid, 32, smem, s>>>(ri, n_rays, L, pads, o1, o2, counts, caps);
 }
 
 __global__ void k_build_up(const float4* csph, const float4* ccone, const unsigned* counts, unsigned level_idx,
@@ -382,16 +399,21 @@ crsh_status build_launch(const crsh_rays* rays, const uint32_t* n_rays, const cr
     RaysIn ri{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz};
     LevelOut o1{reinterpret_cast<float4*>(h->sphere[0]), reinterpret_cast<float4*>(h->cone[0]),
                 reinterpret_cast<float2*>(h->trig[0]), h->capacity[0]};
-    // B lanes per node: blocks of 128 threads hold 128 / B nodes
-    switch (B) {   // a warp per 32 nodes
-        case 2: launch_build_l1<2>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
-        case 4: launch_build_l1<4>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
-        case 8: launch_build_l1<8>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
-        case 16: launch_build_l1<16>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
-        case 32: launch_build_l1<32>(ri, n_rays, L, pads, o1, h->count, caps, h->capacity[0], s, dev); break;
+    LevelOut o2{nullptr, nullptr, nullptr, 0};
+    if (L >= 2)
+        o2 = LevelOut{reinterpret_cast<float4*>(h->sphere[1]), reinterpret_cast<float4*>(h->cone[1]),
+                      reinterpret_cast<float2*>(h->trig[1]), h->capacity[1]};
+    // a warp per 32 level-1 nodes, which also merges them into level 2
+    switch (B) {
+        case 2: launch_build_l1<2>(ri, n_rays, L, pads, o1, o2, h->count, caps, h->capacity[0], s, dev); break;
+        case 4: launch_build_l1<4>(ri, n_rays, L, pads, o1, o2, h->count, caps, h->capacity[0], s, dev); break;
+        case 8: launch_build_l1<8>(ri, n_rays, L, pads, o1, o2, h->count, caps, h->capacity[0], s, dev); break;
+        case 16: launch_build_l1<16>(ri, n_rays, L, pads, o1, o2, h->count, caps, h->capacity[0], s, dev); break;
+        case 32: launch_build_l1<32>(ri, n_rays, L, pads, o1, o2, h->count, caps, h->capacity[0], s, dev); break;
         default: return CRSH_ERR_INVALID_ARG;
     }
-    for (unsigned l = 1; l < L; ++l) {
+    // levels 3 and up: B-lane groups over the stored nodes below
+    for (unsigned l = 2; l < L; ++l) {
         LevelOut o{reinterpret_cast<float4*>(h->sphere[l]), reinterpret_cast<float4*>(h->cone[l]),
                    reinterpret_cast<float2*>(h->trig[l]), h->capacity[l]};
         const unsigned blocks = (unsigned)(((size_t)h->capacity[l] * B + 127) / 128);
