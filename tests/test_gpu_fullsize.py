@@ -155,3 +155,38 @@ def test_sort_at_12m_rays_bit_exact(compress):
         assert np.array_equal(got[k].view(np.uint32), rays[k][perm].view(np.uint32)), k
     if compress:
         assert c["chunks"] == oracle.chunk_count(keys)
+
+
+def test_build_at_12m_rays_equals_its_prefix_build():
+    """The level-1 build at 12.8 M rays (800 K nodes: every warp builds several blocks of 32 nodes,
+    which takes the fully unrolled fold and sphere tree and the 16-byte staging loads) against the
+    build of a 153,600-ray prefix of the same sorted rays (one block per warp: the rolled loops):
+    the nodes the two share, at level 1 and at level 2 (merged in the level-1 kernel), are
+    bit-identical, since every node depends on its own rays only."""
+    from paper_2312_06538_gb300 import pipeline as pl
+    w = synthetic.make(3)
+    g = synthetic.tiled_gbuffer(w, 4)
+    npx = g["hit"].shape[0]
+    stream = torch.cuda.current_stream().cuda_stream
+    p = pl.Pipeline(w.scene, max_pixels=npx, n_lights=w.lights.shape[0], bundle=16, levels=4,
+                    ray_capacity=npx * 4, pair_capacity=1 << 16, device="cuda")
+    hp = pl.hash_params(w.hash_lo, w.hash_hi, shadow_cull=w.shadow_cull)
+    bp = pl.build_params(16, 4, w.build_pads())
+    p.hash_sort(p.gbuffer_struct(p.gbuffer_to_device(g)), torch.from_numpy(w.lights).cuda(), hp, stream)
+    p.build(bp, stream)
+    assert p.read_counters()["status"] == 0
+    n = p.n()
+    assert n > 12_000_000
+    big = p.levels_host()
+    P = 16 * 32 * 300
+    q = pl.Pipeline(w.scene, max_pixels=1, n_lights=w.lights.shape[0], bundle=16, levels=4, ray_capacity=P,
+                    pair_capacity=1 << 16, device="cuda")
+    for k in pl.RAY_FIELDS:
+        q.rays_t[k][:P].copy_(p.rays_t[k][:P])
+    q.n_rays.fill_(P)
+    q.build(bp, stream)
+    small = q.levels_host()
+    assert small[0][0].shape[0] == P // 16 and small[1][0].shape[0] == P // 256
+    for lvl, m in ((0, P // 16), (1, P // 256)):
+        for a, b in zip(big[lvl], small[lvl]):
+            assert np.array_equal(a[:m].view(np.uint32), b[:m].view(np.uint32)), lvl
