@@ -217,7 +217,7 @@ __device__ __forceinline__ unsigned pixel_rays(const crsh_gbuffer& g, unsigned p
 struct GenOut {
     float4* rec;     // 2 per ray
     uint32_t* key;   // generation-order keys
-    uint32_t* val;   // = generation index
+    uint32_t* val;   // sort values: written by the radix passes only (the generation index is implicit)
     uint32_t capacity;
 };
 
@@ -226,7 +226,6 @@ __device__ __forceinline__ void store_ray(const GenOut& o, unsigned pos, const G
     o.rec[2 * (size_t)pos] = make_float4(r.o[0], r.o[1], r.o[2], r.d[0]);
     o.rec[2 * (size_t)pos + 1] = make_float4(r.d[1], r.d[2], r.tmax, __uint_as_float(pixel));
     o.key[pos] = key;
-    o.val[pos] = pos;
 }
 
 constexpr int GEN_BLOCK = 256;
@@ -374,7 +373,7 @@ __device__ __forceinline__ void count_digits(unsigned (*s_h)[256], unsigned k, b
 }
 
 __global__ void __launch_bounds__(CMP_BLOCK) k_chunk(const uint32_t* key, const unsigned* n_ptr, uint32_t* ckey,
-                                                     uint32_t* cval, uint32_t* cbase, unsigned* c_out,
+                                                     uint32_t* cbase, unsigned* c_out,
                                                      unsigned* hist, unsigned long long* status, unsigned* tile_ctr,
                                                      crsh_counters* ctr) {
     __shared__ unsigned s_tile;
@@ -443,7 +442,6 @@ __global__ void __launch_bounds__(CMP_BLOCK) k_chunk(const uint32_t* key, const 
                 unsigned pos = (unsigned)s_prefix + s_cnt[i][warp] + __popc(bal[i] & lanemask_lt());
                 unsigned e = tile * CMP_TILE + i * CMP_BLOCK + threadIdx.x;
                 ckey[pos] = k[i];
-                cval[pos] = pos;
                 cbase[pos] = e;
             }
             count_digits(s_h, f[i] ? k[i] : 0u, f[i]);
@@ -485,7 +483,7 @@ __global__ void k_radix_hist(const uint32_t* key, const unsigned* n_ptr, unsigne
 // buffer (0 = A, 1 = B); plan[4] = buffer holding the sorted result.
 // offs[p][d] = keys with a smaller digit d at pass p.
 __global__ void k_radix_plan(const unsigned* hist, const unsigned* n_ptr, unsigned* offs, unsigned* plan,
-                             int sort_enabled) {
+                             int sort_enabled, int identity) {
     __shared__ unsigned s_triv[4];
     const unsigned n = *n_ptr;
     const int d = threadIdx.x;   // 256 threads
@@ -510,6 +508,11 @@ __global__ void k_radix_plan(const unsigned* hist, const unsigned* n_ptr, unsign
             if (!sort_enabled || s_triv[p]) plan[p] = 0;
             else { plan[p] = 1 + cur; cur ^= 1u; }
         }
+        // identity values exist only inside the first pass: keep one
+        if (sort_enabled && identity && cur == 0 && plan[0] == 0 && plan[1] == 0 && plan[2] == 0 && plan[3] == 0) {
+            plan[0] = 1;
+            cur = 1;
+        }
         plan[4] = cur;
     }
 }
@@ -522,11 +525,14 @@ __global__ void k_radix_plan(const unsigned* hist, const unsigned* n_ptr, unsign
 // in that local order: consecutive threads write consecutive positions of one
 // digit's run, so the stores are coalesced.
 __device__ __forceinline__ void radix_pass_body(int pass, uint32_t* kA, uint32_t* vA, uint32_t* kB,
-                                                         uint32_t* vB, const unsigned* n_ptr, const unsigned* offs,
-                                                         const unsigned* plan, unsigned* status,
-                                                         unsigned* tile_ctr, crsh_counters* ctr) {
+                                                uint32_t* vB, const unsigned* n_ptr, const unsigned* offs,
+                                                const unsigned* plan, unsigned* status, unsigned* tile_ctr,
+                                                crsh_counters* ctr, int identity) {
     const unsigned pl = plan[pass];
     if (pl == 0) return;
+    // identity values (element index) are made, not read, by the first pass that runs
+    bool first = identity != 0;
+    for (int q = 0; q < pass; ++q) first = first && plan[q] == 0;
     const uint32_t* sk = (pl == 1) ? kA : kB;
     const uint32_t* sv = (pl == 1) ? vA : vB;
     uint32_t* dk = (pl == 1) ? kB : kA;
@@ -557,7 +563,7 @@ __device__ __forceinline__ void radix_pass_body(int pass, uint32_t* kA, uint32_t
             const unsigned e = wbase + r * 32 + lane;
             const bool valid = e < cnt;
             key[r] = valid ? sk[t0 + e] : 0u;
-            val[r] = valid ? sv[t0 + e] : 0u;
+            val[r] = valid ? (first ? t0 + e : sv[t0 + e]) : 0u;
         }
 #pragma unroll
         for (int r = 0; r < RS_KPT; ++r) {
@@ -620,15 +626,15 @@ __device__ __forceinline__ void radix_pass_body(int pass, uint32_t* kA, uint32_t
 __global__ void __launch_bounds__(RS_BLOCK) k_radix_pass(int pass, uint32_t* kA, uint32_t* vA, uint32_t* kB,
                                                          uint32_t* vB, const unsigned* n_ptr, const unsigned* offs,
                                                          const unsigned* plan, unsigned* status,
-                                                         unsigned* tile_ctr, crsh_counters* ctr) {
-    radix_pass_body(pass, kA, vA, kB, vB, n_ptr, offs, plan, status, tile_ctr, ctr);
+                                                         unsigned* tile_ctr, crsh_counters* ctr, int identity) {
+    radix_pass_body(pass, kA, vA, kB, vB, n_ptr, offs, plan, status, tile_ctr, ctr, identity);
 }
 __global__ void __launch_bounds__(RS_BLOCK, 3) k_radix_pass_3(int pass, uint32_t* kA, uint32_t* vA, uint32_t* kB,
                                                               uint32_t* vB, const unsigned* n_ptr,
                                                               const unsigned* offs, const unsigned* plan,
                                                               unsigned* status, unsigned* tile_ctr,
-                                                              crsh_counters* ctr) {
-    radix_pass_body(pass, kA, vA, kB, vB, n_ptr, offs, plan, status, tile_ctr, ctr);
+                                                              crsh_counters* ctr, int identity) {
+    radix_pass_body(pass, kA, vA, kB, vB, n_ptr, offs, plan, status, tile_ctr, ctr, identity);
 }
 static_assert(RS_BLOCK == 256, "one thread per digit");
 
@@ -641,10 +647,11 @@ size_t radix_status_words(uint32_t cap) {
 // rw.hist, rw.tile_ctr (4) and rw.status must be zero; rw.plan[4] tells which
 // buffer holds the result (0: A, 1: B).
 void radix_sort_launch(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, const unsigned* cnt_ptr, uint32_t cap,
-                       const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev, bool counted) {
+                       const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev, bool counted,
+                       bool identity) {
     const unsigned cap_tiles = (cap + RS_TILE - 1) / RS_TILE;
     if (!counted) k_radix_hist<<<dev.sms * 2, 256, 0, s>>>(kA, cnt_ptr, rw.hist);
-    k_radix_plan<<<1, 256, 0, s>>>(rw.hist, cnt_ptr, rw.offs, rw.plan, 1);
+    k_radix_plan<<<1, 256, 0, s>>>(rw.hist, cnt_ptr, rw.offs, rw.plan, 1, identity ? 1 : 0);
     const unsigned grid = cap_tiles < (unsigned)(dev.sms * 4) ? (cap_tiles ? cap_tiles : 1) : dev.sms * 4;
     const size_t rs_tiles = (size_t)cap_tiles + 1;
     const bool big = cap >= (1u << 24);
@@ -652,10 +659,10 @@ void radix_sort_launch(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, c
         unsigned* st = rw.status + (size_t)p * rs_tiles * 256;
         if (big)
             k_radix_pass_3<<<grid, RS_BLOCK, 0, s>>>(p, kA, vA, kB, vB, cnt_ptr, rw.offs, rw.plan, st,
-                                                     &rw.tile_ctr[p], ctr);
+                                                     &rw.tile_ctr[p], ctr, identity ? 1 : 0);
         else
             k_radix_pass<<<grid, RS_BLOCK, 0, s>>>(p, kA, vA, kB, vB, cnt_ptr, rw.offs, rw.plan, st,
-                                                   &rw.tile_ctr[p], ctr);
+                                                   &rw.tile_ctr[p], ctr, identity ? 1 : 0);
     }
 }
 
@@ -945,17 +952,17 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
     if (compress) {
         unsigned tiles = (cap + CMP_TILE - 1) / CMP_TILE;
         unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
-        k_chunk<<<grid, CMP_BLOCK, 0, s>>>(w.gen.key, n_out, w.chK, w.chV, w.chBase, &w.counts[0], w.hist,
-                                           w.st_chunk, &w.tile_ctr[1], ctr);
+        k_chunk<<<grid, CMP_BLOCK, 0, s>>>(w.gen.key, n_out, w.chK, w.chBase, &w.counts[0], w.hist, w.st_chunk,
+                                           &w.tile_ctr[1], ctr);
         kA = w.chK;
         vA = w.chV;
         cnt_ptr = &w.counts[0];
     }
     if (sort) {
         RadixWs rw{w.hist, w.offs, w.plan, &w.tile_ctr[2], w.st_radix};
-        radix_sort_launch(kA, vA, w.altK, w.altV, cnt_ptr, cap, rw, ctr, s, dev, compress);
+        radix_sort_launch(kA, vA, w.altK, w.altV, cnt_ptr, cap, rw, ctr, s, dev, compress, true);
     } else {
-        k_radix_plan<<<1, 256, 0, s>>>(w.hist, cnt_ptr, w.offs, w.plan, 0);
+        k_radix_plan<<<1, 256, 0, s>>>(w.hist, cnt_ptr, w.offs, w.plan, 0, 0);
     }
     if (compress) {
         unsigned tiles = (cap + SCAN_TILE - 1) / SCAN_TILE;

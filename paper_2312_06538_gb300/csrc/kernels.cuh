@@ -51,9 +51,11 @@ struct RadixWs {
 };
 size_t radix_status_words(uint32_t cap);
 // counted: rw.hist already holds the digit counts of the keys (their producer made them).
+// identity: the values are the element indices 0 .. n-1; vA is not read (the first pass that
+// runs makes them, and one pass always runs).
 void radix_sort_launch(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, const unsigned* cnt_ptr, uint32_t cap,
                        const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev,
-                       bool counted = false);
+                       bool counted = false, bool identity = false);
 
 size_t hash_sort_workspace(uint32_t capacity, uint32_t max_pixels);
 crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, const float* lights, uint32_t n_lights,
