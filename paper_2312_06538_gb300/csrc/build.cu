@@ -183,6 +183,7 @@ struct Caps {
 template <int B>
 __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_ptr, unsigned L, Pads pads,
                                                  LevelOut out, LevelOut out2, unsigned* counts, Caps caps) {
+    pdl_wait();
     constexpr unsigned S = B + 1, W = 32 * S;
     // 4 x W floats: three staged components (directions for the cone, then
     // origins for the sphere) and the sphere radii; staging the two halves in
@@ -351,11 +352,12 @@ static void launch_build_l1(const RaysIn& ri, const uint32_t* n_rays, unsigned L
     const size_t smem = 4 * 32 * (B + 1) * sizeof(float);
     const unsigned blocks = (cap0 + 31) / 32;
     const unsigned grid = blocks < (unsigned)dev.sms * 32 ? (blocks ? blocks : 1) : dev.sms * 32;
-    k_build_l1<B><<<grid, 32, smem, s>>>(ri, n_rays, L, pads, o1, o2, counts, caps);
+    launch_pdl(k_build_l1<B>, grid, 32, smem, s, ri, n_rays, L, pads, o1, o2, counts, caps);
 }
 
 __global__ void k_build_up(const float4* csph, const float4* ccone, const unsigned* counts, unsigned level_idx,
                            unsigned B, Pads pads, LevelOut out) {
+    pdl_wait();
     const unsigned below = counts[level_idx - 1];
     const unsigned cnt = counts[level_idx];
     const unsigned lane = threadIdx.x & 31, r = lane & (B - 1);
@@ -418,7 +420,7 @@ crsh_status build_launch(const crsh_rays* rays, const uint32_t* n_rays, const cr
                    reinterpret_cast<float2*>(h->trig[l]), h->capacity[l]};
         const unsigned blocks = (unsigned)(((size_t)h->capacity[l] * B + 127) / 128);
         const unsigned grid = blocks < (unsigned)dev.sms * 16 ? (blocks ? blocks : 1) : dev.sms * 16;
-        k_build_up<<<grid, 128, 0, s>>>(reinterpret_cast<const float4*>(h->sphere[l - 1]),
+        launch_pdl(k_build_up, grid, 128, 0, s, reinterpret_cast<const float4*>(h->sphere[l - 1]),
                                         reinterpret_cast<const float4*>(h->cone[l - 1]), h->count, l, B, pads, o);
     }
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;

@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen_gbuffer(crsh_gbuffer g, const
                                                            int cull, HashDev h, GenOut out, unsigned* n_out,
                                                            unsigned long long* status, unsigned* tile_ctr,
                                                            crsh_counters* ctr) {
+    pdl_wait();
     __shared__ unsigned s_tile;
     __shared__ unsigned s_cnt[GEN_SUB][GEN_BLOCK / 32];
     __shared__ unsigned long long s_prefix;
@@ -305,6 +306,7 @@ __global__ void __launch_bounds__(GEN_BLOCK) k_gen_gbuffer(crsh_gbuffer g, const
 
 // Prebuilt rays: hash and copy (every input is a ray, order kept).
 __global__ void k_gen_rays(crsh_rays_in in, HashDev h, GenOut out, unsigned* n_out, crsh_counters* ctr) {
+    pdl_wait();
     const unsigned n = min(in.n, out.capacity);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->rays = in.n;
@@ -331,6 +333,7 @@ __global__ void k_gen_rays(crsh_rays_in in, HashDev h, GenOut out, unsigned* n_o
 // for j < M, each evaluated in FP64 from the same FP64 argument expression as
 // the definition and rounded to FP32; one thread per entry.
 __global__ void k_tables(TableSpec t) {
+    pdl_wait();
     const double pi = 3.14159265358979323846;
     unsigned total = 0;
     for (int i = 0; i < 4; ++i) total += t.n[i];
@@ -346,7 +349,7 @@ void tables_launch(const TableSpec& t, cudaStream_t s, const DeviceInfo& dev) {
     const unsigned total = t.n[0] + t.n[1] + t.n[2] + t.n[3];
     const unsigned blocks = (total + 255) / 256;
     const unsigned grid = blocks < (unsigned)dev.sms ? (blocks ? blocks : 1) : dev.sms;
-    k_tables<<<grid, 256, 0, s>>>(t);
+    launch_pdl(k_tables, grid, 256, 0, s, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -376,6 +379,7 @@ __global__ void __launch_bounds__(CMP_BLOCK) k_chunk(const uint32_t* key, const 
                                                      uint32_t* cbase, unsigned* c_out,
                                                      unsigned* hist, unsigned long long* status, unsigned* tile_ctr,
                                                      crsh_counters* ctr) {
+    pdl_wait();
     __shared__ unsigned s_tile;
     __shared__ unsigned s_cnt[CMP_ITEMS][CMP_BLOCK / 32];
     __shared__ unsigned long long s_prefix;
@@ -461,6 +465,7 @@ static_assert(CMP_PER * 32 == CMP_ITEMS * (CMP_BLOCK / 32), "one warp scans the 
 constexpr int RS_BLOCK = 256, RS_WARPS = RS_BLOCK / 32, RS_KPT = 16, RS_TILE = RS_BLOCK * RS_KPT;
 
 __global__ void k_radix_hist(const uint32_t* key, const unsigned* n_ptr, unsigned* hist /* 4 x 256 */) {
+    pdl_wait();
     __shared__ unsigned s_h[4][256];
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&s_h[0][0])[i] = 0;
     __syncthreads();
@@ -484,6 +489,7 @@ __global__ void k_radix_hist(const uint32_t* key, const unsigned* n_ptr, unsigne
 // offs[p][d] = keys with a smaller digit d at pass p.
 __global__ void k_radix_plan(const unsigned* hist, const unsigned* n_ptr, unsigned* offs, unsigned* plan,
                              int sort_enabled, int identity) {
+    pdl_wait();
     __shared__ unsigned s_triv[4];
     const unsigned n = *n_ptr;
     const int d = threadIdx.x;   // 256 threads
@@ -528,6 +534,7 @@ __device__ __forceinline__ void radix_pass_body(int pass, uint32_t* kA, uint32_t
                                                 uint32_t* vB, const unsigned* n_ptr, const unsigned* offs,
                                                 const unsigned* plan, unsigned* status, unsigned* tile_ctr,
                                                 crsh_counters* ctr, int identity) {
+    pdl_wait();
     const unsigned pl = plan[pass];
     if (pl == 0) return;
     // identity values (element index) are made, not read, by the first pass that runs
@@ -650,18 +657,18 @@ void radix_sort_launch(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, c
                        const RadixWs& rw, crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev, bool counted,
                        bool identity) {
     const unsigned cap_tiles = (cap + RS_TILE - 1) / RS_TILE;
-    if (!counted) k_radix_hist<<<dev.sms * 2, 256, 0, s>>>(kA, cnt_ptr, rw.hist);
-    k_radix_plan<<<1, 256, 0, s>>>(rw.hist, cnt_ptr, rw.offs, rw.plan, 1, identity ? 1 : 0);
+    if (!counted) launch_pdl(k_radix_hist, dev.sms * 2, 256, 0, s, kA, cnt_ptr, rw.hist);
+    launch_pdl(k_radix_plan, 1, 256, 0, s, rw.hist, cnt_ptr, rw.offs, rw.plan, 1, identity ? 1 : 0);
     const unsigned grid = cap_tiles < (unsigned)(dev.sms * 4) ? (cap_tiles ? cap_tiles : 1) : dev.sms * 4;
     const size_t rs_tiles = (size_t)cap_tiles + 1;
     const bool big = cap >= (1u << 24);
     for (int p = 0; p < 4; ++p) {
         unsigned* st = rw.status + (size_t)p * rs_tiles * 256;
         if (big)
-            k_radix_pass_3<<<grid, RS_BLOCK, 0, s>>>(p, kA, vA, kB, vB, cnt_ptr, rw.offs, rw.plan, st,
+            launch_pdl(k_radix_pass_3, grid, RS_BLOCK, 0, s, p, kA, vA, kB, vB, cnt_ptr, rw.offs, rw.plan, st,
                                                      &rw.tile_ctr[p], ctr, identity ? 1 : 0);
         else
-            k_radix_pass<<<grid, RS_BLOCK, 0, s>>>(p, kA, vA, kB, vB, cnt_ptr, rw.offs, rw.plan, st,
+            launch_pdl(k_radix_pass, grid, RS_BLOCK, 0, s, p, kA, vA, kB, vB, cnt_ptr, rw.offs, rw.plan, st,
                                                    &rw.tile_ctr[p], ctr, identity ? 1 : 0);
     }
 }
@@ -697,6 +704,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_pos(const uint32_t* kA, co
                                                           uint32_t* cpos, uint32_t* sbase,
                                                           unsigned long long* status, unsigned* tile_ctr,
                                                           crsh_counters* ctr) {
+    pdl_wait();
     __shared__ unsigned s_tile;
     __shared__ unsigned s_warp[SCAN_BLOCK / 32];
     __shared__ unsigned long long s_prefix;
@@ -779,6 +787,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_chunk_pos(const uint32_t* kA, co
 __global__ void k_gather(int mode, GenOut gen, const uint32_t* kA, const uint32_t* vA, const uint32_t* kB,
                          const uint32_t* vB, const unsigned* plan, const uint32_t* sbase, const uint32_t* cpos,
                          const unsigned* c_ptr, const unsigned* n_ptr, SortedOut out) {
+    pdl_wait();
     const unsigned n = *n_ptr;
     const uint32_t* sv = (mode != 0 && plan[4]) ? vB : vA;
     const uint32_t* sk = (mode != 0 && plan[4]) ? kB : kA;
@@ -936,13 +945,13 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
     if (gb) {
         const unsigned tiles = (gb->n_pixels + GEN_TILE - 1) / GEN_TILE;
         const unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
-        k_gen_gbuffer<<<grid, GEN_BLOCK, 0, s>>>(*gb, lights, n_lights, (int)hp->shadow_cull, h, w.gen, n_out,
+        launch_pdl(k_gen_gbuffer, grid, GEN_BLOCK, 0, s, *gb, lights, n_lights, (int)hp->shadow_cull, h, w.gen, n_out,
                                                  w.st_gen, &w.tile_ctr[0], ctr);
     } else {
         unsigned blocks = (in->n + 255) / 256;
         if (blocks > (unsigned)persist) blocks = persist;
         if (blocks == 0) blocks = 1;
-        k_gen_rays<<<blocks, 256, 0, s>>>(*in, h, w.gen, n_out, ctr);
+        launch_pdl(k_gen_rays, blocks, 256, 0, s, *in, h, w.gen, n_out, ctr);
     }
 
     const bool sort = hp->sort != 0;
@@ -952,7 +961,7 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
     if (compress) {
         unsigned tiles = (cap + CMP_TILE - 1) / CMP_TILE;
         unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
-        k_chunk<<<grid, CMP_BLOCK, 0, s>>>(w.gen.key, n_out, w.chK, w.chBase, &w.counts[0], w.hist, w.st_chunk,
+        launch_pdl(k_chunk, grid, CMP_BLOCK, 0, s, w.gen.key, n_out, w.chK, w.chBase, &w.counts[0], w.hist, w.st_chunk,
                                            &w.tile_ctr[1], ctr);
         kA = w.chK;
         vA = w.chV;
@@ -962,12 +971,12 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
         RadixWs rw{w.hist, w.offs, w.plan, &w.tile_ctr[2], w.st_radix};
         radix_sort_launch(kA, vA, w.altK, w.altV, cnt_ptr, cap, rw, ctr, s, dev, compress, true);
     } else {
-        k_radix_plan<<<1, 256, 0, s>>>(w.hist, cnt_ptr, w.offs, w.plan, 0, 0);
+        launch_pdl(k_radix_plan, 1, 256, 0, s, w.hist, cnt_ptr, w.offs, w.plan, 0, 0);
     }
     if (compress) {
         unsigned tiles = (cap + SCAN_TILE - 1) / SCAN_TILE;
         unsigned grid = tiles < (unsigned)persist ? (tiles ? tiles : 1) : (unsigned)persist;
-        k_chunk_pos<<<grid, SCAN_BLOCK, 0, s>>>(kA, vA, w.altK, w.altV, w.plan, w.chBase, cnt_ptr, w.chPos, w.chSB,
+        launch_pdl(k_chunk_pos, grid, SCAN_BLOCK, 0, s, kA, vA, w.altK, w.altV, w.plan, w.chBase, cnt_ptr, w.chPos, w.chSB,
                                                  w.st_pos, &w.tile_ctr[6], ctr);
     }
     SortedOut so{out->ox, out->oy, out->oz, out->dx, out->dy, out->dz, out->tmax, out->type,
@@ -977,7 +986,7 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
         if (blocks > (unsigned)dev.sms * 4) blocks = dev.sms * 4;
         if (blocks == 0) blocks = 1;
         const int mode = !sort ? 0 : (compress ? 2 : 1);
-        k_gather<<<blocks, 256, 0, s>>>(mode, w.gen, kA, vA, w.altK, w.altV, w.plan, w.chSB, w.chPos, cnt_ptr,
+        launch_pdl(k_gather, blocks, 256, 0, s, mode, w.gen, kA, vA, w.altK, w.altV, w.plan, w.chSB, w.chPos, cnt_ptr,
                                         n_out, so);
     }
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;

@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(CH_BLOCK, 6) k_closest(const uint32_t* pnode, 
                                                          RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
                                                          unsigned long long* best, unsigned* work,
                                                          crsh_counters* ctr) {
+    pdl_wait();
     constexpr int H = B / 2;            // lanes per node (two rays each)
     constexpr int S = 32 / H;           // streams
     // one 64-byte record per triangle: a lane's four copies land side by side
@@ -328,6 +329,7 @@ __global__ void __launch_bounds__(CH_BLOCK, 6) k_closest(const uint32_t* pnode, 
 }
 
 __global__ void k_fill_best(unsigned long long* best, const unsigned* n_ptr, unsigned* work) {
+    pdl_wait();
     const unsigned n = *n_ptr;
     if (work && blockIdx.x == 0 && threadIdx.x == 0) *work = 0;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) best[i] = NO_HIT;
@@ -411,6 +413,7 @@ __device__ __forceinline__ void mt_refine(float ox, float oy, float oz, float dx
 // winner's (t, u, v) from the double-word refinement; scatter to ray_id order
 __global__ void k_finalize(RaysDev rays, const unsigned* n_ptr, crsh_scene sc, const unsigned long long* best,
                            crsh_hits out) {
+    pdl_wait();
     const unsigned n = *n_ptr;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const unsigned long long k = best[i];
@@ -490,7 +493,7 @@ static void launch_closest(const crsh_pairs* pairs, const RaysDev& rd, const uin
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_closest<B>, CH_BLOCK, 0) != cudaSuccess || b <= 0) b = 1;
         per_sm[d].store(b, std::memory_order_relaxed);
     }
-    k_closest<B><<<dev.sms * b, CH_BLOCK, 0, s>>>(pairs->node, pairs->tri, pairs->count, pairs->capacity, rd,
+    launch_pdl(k_closest<B>, dev.sms * b, CH_BLOCK, 0, s, pairs->node, pairs->tri, pairs->count, pairs->capacity, rd,
                                                          n_rays, mt, best, work, ctr);
 }
 
@@ -505,7 +508,7 @@ crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, c
         if (cudaMemsetAsync(c0, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) return CRSH_ERR_CUDA;
     }
     const unsigned fb = dev.sms * 8;
-    k_fill_best<<<fb, 256, 0, s>>>(best, n_rays, work);
+    launch_pdl(k_fill_best, fb, 256, 0, s, best, n_rays, work);
     const RaysDev rd = rays_dev(rays);
     const float4* mt = reinterpret_cast<const float4*>(sc->tri_mt);
     switch (h->bundle) {
@@ -516,7 +519,7 @@ crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, c
         case 32: launch_closest<32>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
         default: return CRSH_ERR_INVALID_ARG;
     }
-    k_finalize<<<fb, 256, 0, s>>>(rd, n_rays, *sc, best, *out);
+    launch_pdl(k_finalize, fb, 256, 0, s, rd, n_rays, *sc, best, *out);
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
 }
 
@@ -529,7 +532,7 @@ crsh_status bruteforce_launch(const crsh_rays* rays, const uint32_t* n_rays, con
     const unsigned blocks = (rays->capacity + BF_BLOCK - 1) / BF_BLOCK;
     const unsigned grid = blocks < (unsigned)dev.sms * 8 ? (blocks ? blocks : 1) : dev.sms * 8;
     k_brute<<<grid, BF_BLOCK, 0, s>>>(rd, n_rays, mt, sc->n_tris, best);
-    k_finalize<<<dev.sms * 8, 256, 0, s>>>(rd, n_rays, *sc, best, *out);
+    launch_pdl(k_finalize, dev.sms * 8, 256, 0, s, rd, n_rays, *sc, best, *out);
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
 }
 
