@@ -2,19 +2,23 @@
 // level-1 (node, triangle) pairs, closest hit per ray; and the N x M brute
 // force of Section 1 built on the same test, for comparison.
 //
-// GB300 design.  The level-1 pair list is cut into fixed chunks of pairs, one
-// per warp task, so long and short triangle lists balance across the 152 SMs.
-// In a warp, lane = (ray slot r < B, stream s < 32/B): the B rays of the
-// current node sit in registers; a group of up to 32 triangles of that node is
-// fetched once (one triangle per lane, 48 bytes, L2-resident) into shared
-// memory and each stream walks every (32/B)-th triangle against its ray.  The
-// per-ray best is a packed (t bits, triangle id) 64-bit key, reduced across
-// streams by shuffles and published with one atomicMin per ray per chunk, so
-// the result does not depend on scheduling.  A last pass recomputes (t, u, v)
-// of the winning triangle with the same test and scatters hits to the rays'
-// generation order.  Decisions (which triangle is closest) are FP32; the
-// reported (t, u, v) of the winner are recomputed in double-word (float +
-// float) arithmetic from the FP32 inputs.
+// GB300 design.  Warps claim fixed chunks of the node-sorted pair list from a
+// counter, so long and short triangle lists balance across the 152 SMs, and
+// walk them in groups of up to 32 pairs of one node.  In a warp, lane =
+// (ray slot r < B/2, stream s < 64/B): each lane holds two of the node's rays
+// (slots r and r + B/2) in registers; a group's triangle records (64 bytes
+// each, L2-resident) are copied into shared memory while the previous group
+// is tested, and each stream walks every (64/B)-th triangle against both of
+// its rays.  Every candidate first gets a ray-line vs triangle-sphere
+// pre-test (paired FP32 operations, two rays per instruction); the few
+// survivors run Moller-Trumbore.  The per-ray best is a packed (t bits,
+// triangle id) 64-bit key, reduced across streams by shuffles and published
+// with one atomicMin per ray per node run, so the result does not depend on
+// scheduling.  A last pass recomputes (t, u, v) of each ray's winning
+// triangle and scatters hits to the rays' generation order.  Decisions
+// (which triangle is closest) are FP32; the reported (t, u, v) of the winner
+// are recomputed in double-word (float + float) arithmetic from the FP32
+// inputs.
 #include <atomic>
 #include <mutex>
 
