@@ -255,3 +255,27 @@ def test_prebuilt_rays_input():
     assert np.array_equal(got["ray_id"], ref["perm"])
     assert np.array_equal(got["pixel"], ref["perm"])        # input index
     parity.check_report(parity.compare_hits(p.hits_host(), ref["hits"], ref["rays"], w.scene.verts))
+
+
+@pytest.mark.parametrize("compress", [True, False])
+def test_all_keys_equal_sort_is_stable(compress):
+    """Keys that are all equal (one ray; many copies of one ray) leave every radix digit trivial, so
+    no pass would move anything: the sort still hands back the rays in input order (the values the
+    first pass makes), with one chunk when compressed."""
+    from paper_2312_06538_gb300 import pipeline as pl
+    w = synthetic.make(2, res=80)
+    ref = _oracle(w)
+    p = pl.workload_pipeline(w)
+    hp = pl.hash_params(w.hash_lo, w.hash_hi, shadow_cull=w.shadow_cull, compress=compress)
+    stream = torch.cuda.current_stream().cuda_stream
+    for n in (1, 300):
+        dev = {k: torch.from_numpy(np.ascontiguousarray(np.repeat(ref["rays"][k][:1], n))).cuda()
+               for k in oracle.RAY_FIELDS + ("type", "light")}
+        p.hash_sort(None, None, hp, stream, rays_in=p.rays_in_struct(dev))
+        c = p.read_counters()
+        assert c["status"] == 0 and c["rays"] == n and p.n() == n
+        got = p.sorted_rays()
+        assert np.array_equal(got["ray_id"], np.arange(n, dtype=np.uint32))
+        assert np.all(got["keys"] == got["keys"][0])
+        if compress:
+            assert c["chunks"] == 1
