@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
             const float4* vy = reinterpret_cast<const float4*>(ay + (size_t)j0 * B);
             const float4* vz = reinterpret_cast<const float4*>(az + (size_t)j0 * B);
 #pragma unroll
-            for (unsigned t = 0; t < B / 4; ++t) {
-                const unsigned q = t * 32 + lane;        // float4 within the block
+            for (int t = 0; t < B / 4; ++t) {
+                const unsigned q = t * 32u + lane;       // float4 within the block
                 const unsigned e = 4 * q, a = (e / B) * S + e % B;
                 const float4 X = vx[q], Y = vy[q], Z = vz[q];
                 s0[a] = X.x; s0[a + 1] = X.y; s0[a + 2] = X.z; s0[a + 3] = X.w;
