@@ -1,14 +1,17 @@
 // Section 3.3.2-3.3.5: secondary ray generation, per-type hashing, trimming,
 // compression into chunks, radix sort of the chunks, decompression.
 //
-// GB300 design: one pass over the G-buffer generates, hashes and trims
-// (stable compaction by decoupled look-back, no second pass over the slots);
-// compression is one more compaction over the keys; the sort is a one-sweep
-// LSD radix sort (8-bit digits, one kernel per digit, digits that are the
-// same for every key skipped on the device) with stable per-warp multisplit
-// ranking; decompression and the gather of the sorted rays are one kernel.
+// GB300 design: one kernel over the G-buffer generates, hashes and trims
+// (each tile counts its pixels' rays, then writes them at the scanned
+// position: stable compaction by decoupled look-back); compression is one
+// more compaction over the keys; the sort is a one-sweep LSD radix sort
+// (8-bit digits, one kernel per digit, digits that are the same for every key
+// skipped on the device) with stable per-warp multisplit ranking, whose first
+// pass makes the sort values (generation or chunk indices) instead of reading
+// them; decompression and the gather of the sorted rays are one kernel.
 // Sizes stay on the device: every kernel runs a persistent grid and reads the
-// count it works on.
+// count it works on; each is launched with programmatic dependent launch and
+// waits on its predecessor before its first access.
 #include "common.cuh"
 #include "kernels.cuh"
 
