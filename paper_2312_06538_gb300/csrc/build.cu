@@ -2,12 +2,15 @@
 // data the traversal and final tests read (triangle bounding spheres,
 // Moller-Trumbore edge layout).
 //
-// GB300 design: a warp builds 32 level-1 nodes.  Rays are staged in shared
-// memory with all loads in flight, then lane k builds node k: the sphere tree
-// (eqs. 7-8) in place and the cone fold (eqs. 1-4).  Upper levels merge their
-// B children in B-lane groups, as balanced trees of shuffle-downs (eqs. 5-8).  Every node is padded outward after its merge so the FP32
-// hierarchy contains its rays, and stores tan(spread), 1/cos(spread) for the
-// eq. 9 tests of the traversal.
+// GB300 design: a warp builds 32 level-1 nodes.  Their rays' directions are
+// staged in shared memory with all loads in flight and lane k folds node k's
+// cone (eqs. 1-4); then the origins go through the same rows and lane k builds
+// the sphere tree (eqs. 7-8) in place.  The warp then merges its 32 nodes into
+// level 2 in B-lane groups; higher levels merge their B children the same way
+// in a kernel per level, as balanced trees of shuffle-downs (eqs. 5-8).  Every
+// node is padded outward after its merge so the FP32 hierarchy contains its
+// rays, and stores tan(spread), 1/cos(spread) for the eq. 9 tests of the
+// traversal.
 #include "common.cuh"
 #include "kernels.cuh"
 
