@@ -264,13 +264,6 @@ crsh_status crsh_shade(const crsh_gbuffer *gb, const float *lights, uint32_t n_l
                        const uint32_t *n_rays, const crsh_hits *hits, const uint32_t *tri_material, float *cells,
                        float *color, void *stream);
 
-/* FP32 peak probe for roofline measurements (not a step of the method):
- * launches `blocks` x 256 threads, each running 8 independent FMA chains for
- * 4 x iters steps, and writes one float per block to `out` (device, `blocks`
- * entries).  *flops (host) receives the FP32 operations launched (2 per FMA);
- * time the call with events on `stream`.  blocks in [1, 2^20], iters >= 1. */
-crsh_status crsh_fma_probe(float *out, uint32_t iters, uint32_t blocks, unsigned long long *flops, void *stream);
-
 /* Library version (major * 10000 + minor * 100 + patch). */
 int crsh_version(void);
 const char *crsh_status_string(crsh_status s);

@@ -104,6 +104,7 @@ SIGNATURES = [
     ("crsh_shade", ctypes.c_int,
      [ctypes.POINTER(crsh_gbuffer), P, U32, ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_hits), P, P, P, P]),
     ("crsh_fma_probe", ctypes.c_int, [P, U32, U32, ctypes.POINTER(ctypes.c_ulonglong), P]),
+    ("crsh_lookback_selftest", ctypes.c_int, [P, P, U32, U32, U32, U32, P, P, P]),
     ("crsh_hash_sort_workspace", ctypes.c_size_t, [U32, U32]),
     ("crsh_hash_sort", ctypes.c_int,
      [ctypes.POINTER(crsh_gbuffer), ctypes.POINTER(crsh_rays_in), P, U32, ctypes.POINTER(crsh_hash_params),
@@ -201,6 +202,14 @@ def crsh_fma_probe(out: int, iters: int, blocks: int, stream: int) -> int:
     f = ctypes.c_ulonglong(0)
     _check("crsh_fma_probe", load().crsh_fma_probe(P(out), iters, blocks, ctypes.byref(f), P(stream)))
     return int(f.value)
+
+
+def crsh_lookback_selftest(status64: int, status32: int, wide: bool, tile: int, aggregate: int, spin_limit: int,
+                           prefix_out: int, counters: int, stream: int):
+    """Diagnostics: one tile's look-back against prepared status words with a bounded wait."""
+    _check("crsh_lookback_selftest",
+           load().crsh_lookback_selftest(P(status64), P(status32), int(bool(wide)), tile, aggregate, spin_limit,
+                                         P(prefix_out), P(counters), P(stream)))
 
 
 def crsh_hash_tables(theta_bits: int, phi_bits: int, cos_out: int, tan_out: int, stream: int):

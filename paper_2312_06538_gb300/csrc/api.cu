@@ -1,10 +1,12 @@
-// C-ABI entry points of include/crsh.h: argument checks (synchronous), device
-// lookup, then the launches in the kernel translation units.
+// C-ABI entry points of include/crsh.h and include/crsh_diag.h: argument
+// checks (synchronous), device lookup, then the launches in the kernel
+// translation units.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "crsh.h"
+#include "crsh_diag.h"
 #include "kernels.cuh"
 
 namespace crsh {
@@ -125,6 +127,18 @@ crsh_status crsh_shade(const crsh_gbuffer* gb, const float* lights, uint32_t n_l
 crsh_status crsh_fma_probe(float* out, uint32_t iters, uint32_t blocks, unsigned long long* flops, void* stream) {
     if (!out || !flops || iters < 1 || blocks < 1 || blocks > (1u << 20)) return CRSH_ERR_INVALID_ARG;
     *flops = fma_probe_launch(out, iters, blocks, static_cast<cudaStream_t>(stream));
+    return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
+}
+
+crsh_status crsh_lookback_selftest(unsigned long long* status64, uint32_t* status32, uint32_t wide, uint32_t tile,
+                                   uint32_t aggregate, uint32_t spin_limit, unsigned long long* prefix_out,
+                                   crsh_counters* counters, void* stream) {
+    if (!prefix_out || !counters || tile < 1 || spin_limit < 1 || spin_limit > (1u << 22)) return CRSH_ERR_INVALID_ARG;
+    if (wide ? !status64 : (!status32 || aggregate >= (1u << 30))) return CRSH_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if (!current_device(dev)) return CRSH_ERR_CUDA;
+    lookback_selftest_launch(status64, status32, wide ? 1 : 0, tile, aggregate, spin_limit, prefix_out, counters,
+                             static_cast<cudaStream_t>(stream));
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
 }
 

@@ -122,8 +122,8 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // block waits for has already been taken by a running block, which publishes
 // its own total before it waits on anyone.  Status word: bits 63:62 flag
 // (0 = not ready, 1 = tile total, 2 = inclusive prefix), bits 61:0 value.
-// Waits are bounded: after kSpinLimit polls the tile records
-// CRSH_ERR_TIMEOUT and continues with what it has.
+// Waits are bounded: after kSpinLimit polls (or the spin_limit a caller
+// passes) the tile records CRSH_ERR_TIMEOUT and continues with what it has.
 
 constexpr unsigned long long LB_AGG = 1ull << 62;
 constexpr unsigned long long LB_INC = 2ull << 62;
@@ -134,7 +134,7 @@ constexpr unsigned kSpinLimit = 1u << 22;
 // (the same in every lane) and publishes the tile's inclusive prefix.
 __device__ __forceinline__ unsigned long long lookback_warp(unsigned long long* status, unsigned tile,
                                                            unsigned long long aggregate,
-                                                           crsh_counters* ctr) {
+                                                           crsh_counters* ctr, unsigned spin_limit = kSpinLimit) {
     const int lane = threadIdx.x & 31;
     if (tile == 0) {
         if (lane == 0) st_relaxed(&status[0], LB_INC | aggregate);
@@ -148,7 +148,7 @@ __device__ __forceinline__ unsigned long long lookback_warp(unsigned long long* 
         long long idx = k - lane;
         unsigned long long s = (idx >= 0) ? ld_relaxed(&status[idx]) : LB_INC;
         while (__any_sync(FULL, (s >> 62) == 0)) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 if (lane == 0) set_status(ctr, CRSH_ERR_TIMEOUT);
                 if ((s >> 62) == 0) s = LB_INC;
                 break;
@@ -191,7 +191,8 @@ __device__ __forceinline__ void lookback32_publish(unsigned* status, unsigned ti
 // After lookback32_publish: the tile's exclusive prefix; publishes its
 // inclusive prefix.
 __device__ __forceinline__ unsigned lookback32_resolve(unsigned* status, unsigned tile, unsigned stride,
-                                                       unsigned aggregate, crsh_counters* ctr) {
+                                                       unsigned aggregate, crsh_counters* ctr,
+                                                       unsigned spin_limit = kSpinLimit) {
     if (tile == 0) return 0;
     unsigned excl = 0;
     unsigned spins = 0;
@@ -216,7 +217,7 @@ __device__ __forceinline__ unsigned lookback32_resolve(unsigned* status, unsigne
         if (done) break;
         k -= used;
         if (used == 0) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 set_status(ctr, CRSH_ERR_TIMEOUT);
                 break;
             }

@@ -155,7 +155,8 @@ __device__ __forceinline__ void flush_best(unsigned long long bk, bool rvalid, i
 template <int B>
 __global__ void __launch_bounds__(CH_BLOCK, 6) k_closest(const uint32_t* pnode, const uint32_t* ptri,
                                                          const unsigned* p_count, unsigned long long p_cap,
-                                                         RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
+                                                         RaysDev rays, const unsigned* n_ptr, unsigned n_cap,
+                                                         const float4* tri_mt,
                                                          unsigned long long* best, unsigned* work,
                                                          crsh_counters* ctr) {
     pdl_wait();
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(CH_BLOCK, 6) k_closest(const uint32_t* pnode, 
     __shared__ __align__(16) float4 s_tri[CH_WARPS][2][32][4];    // (a, n.x) (e1, n.y) (e2, n.z) (c, q)
     __shared__ unsigned s_tid[CH_WARPS][2][32];
     const unsigned P = (unsigned)min((unsigned long long)*p_count, p_cap);
-    const unsigned N = *n_ptr;
+    const unsigned N = min(*n_ptr, n_cap);   // rays past the capacity are never touched
     const unsigned n_chunks = (P + CH_PAIRS - 1) / CH_PAIRS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = lane % H, sidx = lane / H;
@@ -332,10 +333,16 @@ __global__ void __launch_bounds__(CH_BLOCK, 6) k_closest(const uint32_t* pnode, 
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->final_tests_paper = (unsigned long long)P * B;
 }
 
-__global__ void k_fill_best(unsigned long long* best, const unsigned* n_ptr, unsigned* work) {
+// n_cap: rays the scratch and the ray arrays hold; a larger device count is
+// clamped to it and reported as CRSH_ERR_CAPACITY (no access past the end)
+__global__ void k_fill_best(unsigned long long* best, const unsigned* n_ptr, unsigned n_cap, unsigned* work,
+                            crsh_counters* ctr) {
     pdl_wait();
-    const unsigned n = *n_ptr;
-    if (work && blockIdx.x == 0 && threadIdx.x == 0) *work = 0;
+    const unsigned n = min(*n_ptr, n_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (work) *work = 0;
+        if (*n_ptr > n_cap) set_status(ctr, CRSH_ERR_CAPACITY);
+    }
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) best[i] = NO_HIT;
 }
 
@@ -415,10 +422,10 @@ __device__ __forceinline__ void mt_refine(float ox, float oy, float oz, float dx
 }
 
 // winner's (t, u, v) from the double-word refinement; scatter to ray_id order
-__global__ void k_finalize(RaysDev rays, const unsigned* n_ptr, crsh_scene sc, const unsigned long long* best,
-                           crsh_hits out) {
+__global__ void k_finalize(RaysDev rays, const unsigned* n_ptr, unsigned n_cap, crsh_scene sc,
+                           const unsigned long long* best, crsh_hits out) {
     pdl_wait();
-    const unsigned n = *n_ptr;
+    const unsigned n = min(*n_ptr, n_cap);
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const unsigned long long k = best[i];
         const unsigned dst = rays.ray_id[i];
@@ -439,10 +446,10 @@ __global__ void k_finalize(RaysDev rays, const unsigned* n_ptr, crsh_scene sc, c
 
 // N x M: one ray per thread, triangles streamed through shared memory.
 constexpr int BF_BLOCK = 256;
-__global__ void __launch_bounds__(BF_BLOCK) k_brute(RaysDev rays, const unsigned* n_ptr, const float4* tri_mt,
-                                                    unsigned n_tris, unsigned long long* best) {
+__global__ void __launch_bounds__(BF_BLOCK) k_brute(RaysDev rays, const unsigned* n_ptr, unsigned n_cap,
+                                                    const float4* tri_mt, unsigned n_tris, unsigned long long* best) {
     __shared__ float4 s_tri[BF_BLOCK][4];
-    const unsigned n = *n_ptr;
+    const unsigned n = min(*n_ptr, n_cap);
     for (unsigned base = blockIdx.x * BF_BLOCK; base < n; base += gridDim.x * BF_BLOCK) {
         const unsigned i = base + threadIdx.x;
         const bool valid = i < n;
@@ -487,7 +494,8 @@ static RaysDev rays_dev(const crsh_rays* r) {
 // One wave of resident blocks: every warp owns an equal contiguous share of
 // the pairs, so a second partial wave would double the time.
 template <int B>
-static void launch_closest(const crsh_pairs* pairs, const RaysDev& rd, const uint32_t* n_rays, const float4* mt,
+static void launch_closest(const crsh_pairs* pairs, const RaysDev& rd, const uint32_t* n_rays, unsigned n_cap,
+                           const float4* mt,
                            unsigned long long* best, unsigned* work, crsh_counters* ctr, cudaStream_t s,
                            const DeviceInfo& dev) {
     static std::atomic<int> per_sm[64];   // resident blocks per SM, per device
@@ -498,7 +506,7 @@ static void launch_closest(const crsh_pairs* pairs, const RaysDev& rd, const uin
         per_sm[d].store(b, std::memory_order_relaxed);
     }
     launch_pdl(k_closest<B>, dev.sms * b, CH_BLOCK, 0, s, pairs->node, pairs->tri, pairs->count, pairs->capacity, rd,
-                                                         n_rays, mt, best, work, ctr);
+               n_rays, n_cap, mt, best, work, ctr);
 }
 
 crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
@@ -512,18 +520,19 @@ crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, c
         if (cudaMemsetAsync(c0, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) return CRSH_ERR_CUDA;
     }
     const unsigned fb = dev.sms * 8;
-    launch_pdl(k_fill_best, fb, 256, 0, s, best, n_rays, work);
+    const unsigned cap = rays->capacity;
+    launch_pdl(k_fill_best, fb, 256, 0, s, best, n_rays, cap, work, ctr);
     const RaysDev rd = rays_dev(rays);
     const float4* mt = reinterpret_cast<const float4*>(sc->tri_mt);
     switch (h->bundle) {
-        case 2: launch_closest<2>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
-        case 4: launch_closest<4>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
-        case 8: launch_closest<8>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
-        case 16: launch_closest<16>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
-        case 32: launch_closest<32>(pairs, rd, n_rays, mt, best, work, ctr, s, dev); break;
+        case 2: launch_closest<2>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
+        case 4: launch_closest<4>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
+        case 8: launch_closest<8>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
+        case 16: launch_closest<16>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
+        case 32: launch_closest<32>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
         default: return CRSH_ERR_INVALID_ARG;
     }
-    launch_pdl(k_finalize, fb, 256, 0, s, rd, n_rays, *sc, best, *out);
+    launch_pdl(k_finalize, fb, 256, 0, s, rd, n_rays, cap, *sc, best, *out);
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
 }
 
@@ -535,8 +544,8 @@ crsh_status bruteforce_launch(const crsh_rays* rays, const uint32_t* n_rays, con
     const float4* mt = reinterpret_cast<const float4*>(sc->tri_mt);
     const unsigned blocks = (rays->capacity + BF_BLOCK - 1) / BF_BLOCK;
     const unsigned grid = blocks < (unsigned)dev.sms * 8 ? (blocks ? blocks : 1) : dev.sms * 8;
-    k_brute<<<grid, BF_BLOCK, 0, s>>>(rd, n_rays, mt, sc->n_tris, best);
-    launch_pdl(k_finalize, dev.sms * 8, 256, 0, s, rd, n_rays, *sc, best, *out);
+    k_brute<<<grid, BF_BLOCK, 0, s>>>(rd, n_rays, rays->capacity, mt, sc->n_tris, best);
+    launch_pdl(k_finalize, dev.sms * 8, 256, 0, s, rd, n_rays, (unsigned)rays->capacity, *sc, best, *out);
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
 }
 

@@ -38,8 +38,11 @@ crsh_status shade_launch(const crsh_gbuffer* gb, const float* lights, uint32_t n
                          const uint32_t* n_rays, const crsh_hits* hits, const uint32_t* tri_material, float* cells,
                          float* color, cudaStream_t s, const DeviceInfo& dev);
 
-// FP32 FMA throughput probe (probe.cu): returns the flops launched.
+// Diagnostics (diag.cu): the FP32 FMA throughput probe (returns the flops
+// launched) and the bounded-wait self-test of the look-back.
 unsigned long long fma_probe_launch(float* out, unsigned iters, unsigned blocks, cudaStream_t s);
+void lookback_selftest_launch(unsigned long long* s64, unsigned* s32, int wide, unsigned tile, unsigned aggregate,
+                              unsigned spin_limit, unsigned long long* out, crsh_counters* ctr, cudaStream_t s);
 
 // One-sweep LSD radix sort of 32-bit (key, value) pairs (hash_sort.cu).
 struct RadixWs {

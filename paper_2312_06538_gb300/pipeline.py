@@ -204,7 +204,9 @@ class Pipeline:
             self.run(gbuf, lights, hp, bp, mesh_cull)
             c = self.read_counters()
             if c["status"] == C.ERR_CAPACITY and c["needed_pairs"] > self.pair_capacity:
-                self.set_pair_capacity(int(c["needed_pairs"] * 1.25) + 1024)
+                if c["needed_pairs"] > (1 << 31):
+                    raise RuntimeError(f"pair lists of {c['needed_pairs']} entries exceed the 2^31 capacity limit")
+                self.set_pair_capacity(min(int(c["needed_pairs"] * 1.25) + 1024, 1 << 31))
                 continue
             if c["status"] != C.OK:
                 raise C.CrshError("device status", c["status"])

@@ -2,6 +2,7 @@
 include/crsh.h declares, its ctypes structs match the C layout, and argument
 errors come back synchronously before any CUDA work."""
 import ctypes
+import glob
 import os
 import re
 import subprocess
@@ -13,12 +14,15 @@ from paper_2312_06538_gb300 import crsh as C
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "crsh.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(crsh_\w+)\s*\(", text, flags=re.M)
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(crsh_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
@@ -89,6 +93,10 @@ def test_argument_errors_are_synchronous():
     assert lib.crsh_traverse(ctypes.byref(h), ctypes.byref(sc), None, None, None, None, 0, None) == C.ERR_INVALID_ARG
     assert lib.crsh_closest_hit(ctypes.byref(h), ctypes.byref(rays), None, ctypes.byref(sc), None, None, None, None,
                                 0, None) == C.ERR_INVALID_ARG
+    # the look-back self-test: tile 0 has no predecessor, the spin limit must be in [1, 2^22]
+    for tile, limit in ((0, 16), (3, 0), (3, (1 << 22) + 1)):
+        assert lib.crsh_lookback_selftest(P(0x1000), P(0x1000), 1, tile, 1, limit, P(0x1000), P(0x1000),
+                                          None) == C.ERR_INVALID_ARG
 
 
 def test_misaligned_workspace_is_an_argument_error():

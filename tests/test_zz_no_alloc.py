@@ -39,13 +39,11 @@ def test_noalloc_matches_workspace_call_twice_in_a_row():
         c2 = p.read_counters()
         assert c2["status"] == C.OK
         assert c2["final_tests"] == c["final_tests"] and c2["final_hits"] == c["final_hits"]
-        tri, t, u, v = p.hits_host()
-        assert np.array_equal(tri, ref[0])
-        hit = tri >= 0
-        assert np.allclose(t[hit], ref[1][hit], rtol=1e-5, atol=0)
-        assert np.allclose(u[hit], ref[2][hit], rtol=0, atol=1e-5)
-        assert np.allclose(v[hit], ref[3][hit], rtol=0, atol=1e-5)
-        assert (t[~hit] == 0).all()
+        # the same deterministic kernels run on the same inputs: the results are
+        # compared bit for bit, so a scratch-aliasing error of any size shows
+        got = p.hits_host()
+        for x, y in zip(got, ref):
+            assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
 
 
 def test_noalloc_rejects_more_rays_than_its_array_holds():
@@ -60,3 +58,27 @@ def test_noalloc_rejects_more_rays_than_its_array_holds():
                                            C.P(p.counters.data_ptr()), C.P(stream))
     assert rc == C.ERR_INVALID_ARG
     torch.cuda.synchronize()
+
+
+def test_noalloc_clamps_a_device_count_above_the_capacity():
+    """A device ray count larger than rays->capacity must not make the kernels walk past
+    the shared array: they stop at the capacity and report CRSH_ERR_CAPACITY."""
+    from paper_2312_06538_gb300 import crsh as C
+    p, c = _pipeline()
+    ref = [x.copy() for x in p.hits_host()]
+    n = p.n()
+    stream = torch.cuda.current_stream().cuda_stream
+    # slots past the real rays get valid generation indices (the hits are scattered
+    # through them), then the count is raised past the capacity
+    cap = p.ray_capacity
+    p.rays_t["ray_id"][n:cap] = torch.arange(n, cap, dtype=torch.int64, device="cuda").to(torch.uint32)
+    p.n_rays.fill_(cap + 1000)
+    C.crsh_closest_hit_noalloc(p.hier, p.rays, p.n_rays.data_ptr(), p.scene, p.pairs, p.hits,
+                               p.counters.data_ptr(), stream)
+    torch.cuda.synchronize()
+    st = p.read_counters()["status"]
+    p.n_rays.fill_(n)
+    assert st == C.ERR_CAPACITY
+    # the real rays still got their hits
+    got = p.hits_host()
+    assert np.array_equal(got[0], ref[0])
