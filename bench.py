@@ -352,8 +352,7 @@ def comparators(w, p, gstruct, lights, hp, bp, flush, stream, dev, n_rays):
         q = None
         torch.cuda.empty_cache()
         side = min(512, w.width, w.height)
-        g_crop = {k: torch.from_numpy(v).to(dev) for k, v in
-                  pl.Pipeline.gbuffer_to_device(crop_gbuffer(w, side), "cpu").items()}
+        g_crop = pl.Pipeline.gbuffer_to_device(crop_gbuffer(w, side), dev)
         q = pl.Pipeline(w.scene, max_pixels=side * side, n_lights=w.lights.shape[0], bundle=w.bundle,
                         levels=w.levels, device=dev)
         g_rah = q.gbuffer_struct(g_crop)
@@ -663,6 +662,12 @@ def run_gpu(args, w):
     gstruct = p.gbuffer_struct(g_dev)
     c = p.run_fit(gstruct, lights, hp, bp)          # sizes the pair lists, checks the status
     n_rays = c["rays"]
+    if args.profile_steps:
+        # for profilers: the path's calls issued directly, nothing timed or printed
+        for _ in range(args.profile_steps):
+            p.run(gstruct, lights, hp, bp)
+        torch.cuda.synchronize(dev)
+        return
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
@@ -854,6 +859,8 @@ def main():
     ap.add_argument("--ref-crop", type=int, default=64)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run the path this many times after sizing it, time nothing, print nothing (for ncu)")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

@@ -42,10 +42,13 @@ def secondary_rays(scene, gbuffer: Dict[str, np.ndarray], lights: np.ndarray, n:
     out["light"] = torch.zeros(got, dtype=torch.uint8, device=device)
     # light index of shadow rays: shadow slots of a pixel come in light order
     if lights.shape[0] > 1:
-        # recover it from the key (light bits sit above the 26-bit direction code)
+        # recover it from the key: the light bits sit above the shadow direction code
+        # (theta + phi bits of the hash parameters)
+        code_bits = int(hp.shadow_theta_bits) + int(hp.shadow_phi_bits)
+        light_mask = (1 << (30 - code_bits)) - 1
         keys = p.keys[:got].to(torch.int64) & 0xFFFFFFFF
         sh = out["type"] == C.RAY_SHADOW
-        out["light"] = torch.where(sh, (keys >> 26) & 0xF, torch.zeros_like(keys)).to(torch.uint8)
+        out["light"] = torch.where(sh, (keys >> code_bits) & light_mask, torch.zeros_like(keys)).to(torch.uint8)
     del p
     return out, got
 

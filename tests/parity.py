@@ -11,7 +11,12 @@ accepted only in three cases, each counted and reported:
          the kernel's FP32 Cramer-form Moller-Trumbore (below), evaluated per
          ray and triangle, and capped at EDGE_CAP (barycentric units) and
          TMAX_CAP (relative distance): a mismatch outside the capped band is
-         unexplained however grazing the ray;
+         unexplained however grazing the ray.  TMAX_CAP is 10x the 1e-4 by
+         which a shadow ray stops short of its own surface (t_max = 0.9999
+         of the distance): at grazing incidence on small triangles the FP32
+         error of t exceeds that 1e-4, and the kernel may then find the ray's
+         own surface triangle; the cap still rejects any t-range flip more
+         than 1e-3 of the distance away;
 - order: both triangles are hit, and their distances are closer than the
          FP32 error bound of t (capped at ORDER_CAP relative).
 
@@ -41,7 +46,7 @@ T_REL = 1e-5      # hit distance, relative
 UV_ABS = 1e-5     # barycentrics, absolute
 TIE_REL = 1e-6    # two triangles this close in t are a near-tie (either id is correct)
 EDGE_CAP = 1e-3   # largest barycentric band an FP32 edge decision may be excused in
-TMAX_CAP = 1e-5   # largest relative band around t = t_max / t = 0 that may be excused
+TMAX_CAP = 1e-3   # largest relative band around t = t_max / t = 0 that may be excused
 ORDER_CAP = 1e-5  # largest relative t difference an FP32 ordering flip may be excused at
 
 U32 = 2.0 ** -24          # unit roundoff of FP32
