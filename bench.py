@@ -342,22 +342,31 @@ def comparators(w, p, gstruct, lights, hp, bp, flush, stream, dev, n_rays):
                          "tri_tests_per_ray": w.scene.n_tris}
     hp_rah, _ = pl.workload_params(w, sort=False)
     # Unsorted nodes accept far more triangles: the pair lists of the whole frame may not
-    # fit the 2^31-entry pair capacity; then the mode runs on the central 512x512 crop.
+    # fit the 2^31-entry pair capacity; then the mode runs on the largest central crop
+    # (512, 256 or 128 pixels square) whose lists fit.
     sample = "the whole frame"
+    q, c, why = None, None, ""
     try:
         q = pl.workload_pipeline(w, device=dev)
         g_rah = gstruct
         c = q.run_fit(g_rah, lights, hp_rah, bp, mesh_cull=False)
     except Exception as e:
+        why = f"{type(e).__name__} on the whole frame: {e}"
         q = None
+    for side in (512, 256, 128):
+        if c is not None or side > min(w.width, w.height):
+            continue
         torch.cuda.empty_cache()
-        side = min(512, w.width, w.height)
-        g_crop = pl.Pipeline.gbuffer_to_device(crop_gbuffer(w, side), dev)
-        q = pl.Pipeline(w.scene, max_pixels=side * side, n_lights=w.lights.shape[0], bundle=w.bundle,
-                        levels=w.levels, device=dev)
-        g_rah = q.gbuffer_struct(g_crop)
-        c = q.run_fit(g_rah, lights, hp_rah, bp, mesh_cull=False)
-        sample = f"central {side}x{side} crop ({type(e).__name__} on the whole frame: {e})"
+        try:
+            g_crop = pl.Pipeline.gbuffer_to_device(crop_gbuffer(w, side), dev)
+            q = pl.Pipeline(w.scene, max_pixels=side * side, n_lights=w.lights.shape[0], bundle=w.bundle,
+                            levels=w.levels, device=dev)
+            g_rah = q.gbuffer_struct(g_crop)
+            c = q.run_fit(g_rah, lights, hp_rah, bp, mesh_cull=False)
+            sample = f"central {side}x{side} crop ({why})"
+        except Exception as e:
+            why += f"; {type(e).__name__} on the {side}x{side} crop"
+            q = None
     ms = time_path(lambda: q.run(g_rah, lights, hp_rah, bp, mesh_cull=False, stream=sh), flush, stream, reps=5)
     out["unsorted_no_mesh_cull"] = {"mrays_per_s": c["rays"] / (ms * 1e-3) / 1e6, "ms_per_step": ms,
                                     "tri_tests_per_ray": c["final_tests"] / max(1, c["rays"]),
