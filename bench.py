@@ -811,6 +811,11 @@ def run_gpu(args, w):
                    "rays_per_step": n_rays, "bundle": w.bundle, "levels": w.levels,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (512 MiB write outside the step events)"},
+        "level_counts": {"levels": "index l-1 = level l (Tables 1-3 schema)", "tests": list(map(int, c["tests"])),
+                         "hits": list(map(int, c["hits"])), "tests_paper": list(map(int, c["tests_paper"])),
+                         "mesh_tests": int(c["mesh_tests"]), "mesh_hits": int(c["mesh_hits"]),
+                         "final_tests": int(c["final_tests"]), "final_hits": int(c["final_hits"]),
+                         "chunks": int(c["chunks"])},
         "tri_tests_per_ray": c["final_tests"] / max(1, n_rays),
         "all_tests_per_ray": total_tests / max(1, n_rays),
         "bruteforce_tests_per_ray": w.scene.n_tris,

@@ -153,7 +153,7 @@ __device__ __forceinline__ void flush_best(unsigned long long bk, bool rvalid, i
 // pair -> triangle -> record never stalls the tests.  *work must be 0 at
 // launch.
 template <int B>
-__global__ void __launch_bounds__(CH_BLOCK, 6) k_closest(const uint32_t* pnode, const uint32_t* ptri,
+__global__ void __launch_bounds__(CH_BLOCK, 8) k_closest(const uint32_t* pnode, const uint32_t* ptri,
                                                          const unsigned* p_count, unsigned long long p_cap,
                                                          RaysDev rays, const unsigned* n_ptr, unsigned n_cap,
                                                          const float4* tri_mt,

@@ -446,7 +446,7 @@ __device__ __forceinline__ float4 chunk_sphere(float4 ts, bool valid) {
 // that rejects the bounding sphere rejects every triangle sphere inside it
 // (its word is 0) and only the children that accept it run the 32-lane tests.
 template <class Parents>
-__global__ void __launch_bounds__(256, 5) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
+__global__ void __launch_bounds__(256, 6) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
     pdl_wait();
     const WorkSplit ws(sb.totals[0], sb.work + 0, 16u);
     const int lane = threadIdx.x & 31;
