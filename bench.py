@@ -431,33 +431,53 @@ def batched_comparison(dev, n_batches=32, reps=5):
     bat = bt.BatchedCRSH(batches, pads_of, hp_of, tuner=tuner, n_streams=8, device=dev)
     tune_s = time.perf_counter() - t0
     plain = bt.PlainBatches(batches, pads_of, hp_of, device=dev)
+    plain_g = bt.PlainBatches(batches, pads_of, hp_of, device=dev)
+    fixed = bt.BatchedCRSH(batches, pads_of, hp_of, tuner=bt.Autotuner(bundles=(16,), depths=(4,), reps=1, blocks=(256,)),
+                           n_streams=8, device=dev)
     bat.capture()
+    plain_g.capture()
+    fixed.capture()
     total = sum(n for _, _, n in batches)
+    stream = torch.cuda.current_stream(dev)
 
     def timed(fn):
-        torch.cuda.synchronize()
+        """Median of reps, CUDA events on the launching stream (the graph replays run
+        their side streams between the events)."""
         fn()
-        torch.cuda.synchronize()
+        torch.cuda.synchronize(dev)
         ts = []
         for _ in range(reps):
-            torch.cuda.synchronize()
-            t = time.perf_counter()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
             fn()
-            torch.cuda.synchronize()
-            ts.append(time.perf_counter() - t)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b) * 1e-3)
         return sorted(ts)[len(ts) // 2]
     tp = timed(plain.run)
+    tpg = timed(plain_g.replay)
+    tf = timed(fixed.replay)
     tb = timed(bat.replay)
     identical = all(torch.equal(x.view(torch.int32), y.view(torch.int32))
-                    for a, b in zip(bat.runs, plain.runs) for x, y in zip(a.hits(), b.hits()))
+                    for runs in (bat.runs, plain_g.runs, fixed.runs)
+                    for a, b in zip(runs, plain.runs) for x, y in zip(a.hits(), b.hits()))
     out = {"workload": f"{len(batches)} batches, {total:,} rays, sizes {min(n for n, _ in spec)}..{max(n for n, _ in spec)}, "
                        f"8 scenes of 5k..200k triangles",
            "plain_mrays_per_s": total / tp / 1e6, "batched_mrays_per_s": total / tb / 1e6,
            "batched_over_plain": tp / tb, "identical_hits": bool(identical),
-           "plain_ms": 1e3 * tp, "batched_ms": 1e3 * tb, "timing": "host wall clock around the whole set, synchronised",
+           "plain_ms": 1e3 * tp, "batched_ms": 1e3 * tb,
+           "ablation": {
+               "plain_eager_ms": 1e3 * tp,
+               "plain_one_graph_one_stream_ms": 1e3 * tpg,
+               "untuned_B16_L4_graph_8_streams_ms": 1e3 * tf,
+               "tuned_graph_8_streams_ms": 1e3 * tb,
+               "what": "plain calls issued from Python on one stream; the same calls captured in one graph on "
+                       "one stream (removes host launch gaps); every batch at B=16, L=4 in one graph over 8 "
+                       "streams (adds concurrency); the autotuned B, L in that graph (adds tuning)"},
+           "timing": "CUDA events on the launching stream, median of reps",
            "tuned": {str(k): list(v) for k, v in sorted(tuner.table.items())},
            "prep_s": prep_s, "tune_s": tune_s}
-    del bat, plain
+    del bat, plain, plain_g, fixed
     torch.cuda.empty_cache()
     return out
 

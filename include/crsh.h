@@ -149,7 +149,7 @@ typedef struct {
 } crsh_scene;
 
 typedef struct {
-    uint32_t bundle;                 /* B: children per node, power of two in [2, 32] */
+    uint32_t bundle;                 /* B: children per node, power of two in [2, 64] */
     uint32_t levels;                 /* L: levels built and traversed, 1..CRSH_MAX_LEVELS */
     float sphere_pad_rel, sphere_pad_abs;  /* radius -> r (1 + rel) + abs after each node */
     float cone_pad_rel, cone_pad_abs;      /* spread -> s (1 + rel) + abs (radians) */
@@ -167,6 +167,9 @@ typedef struct {
 
 typedef struct {
     uint32_t mesh_cull;              /* 1: whole-mesh spheres at the top level (Section 3.3.7) */
+    uint32_t block_threads;          /* block shape of the traversal's test and emit passes: 128,
+                                        256 or 512 threads (0 = 256); a tuning knob, results do
+                                        not depend on it */
 } crsh_traverse_params;
 
 /* Level-1 (node, triangle) pairs grouped by node, triangles ascending. */

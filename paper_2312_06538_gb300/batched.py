@@ -22,8 +22,9 @@ import torch
 from . import crsh as C
 from .pipeline import Pipeline, RAY_FIELDS, build_params, hash_params
 
-BUNDLES = (4, 8, 16, 32)
-DEPTHS = (2, 3, 4, 5)
+BUNDLES = (4, 8, 16, 32, 64)
+DEPTHS = (2, 3, 4, 5, 6)
+BLOCKS = (128, 256, 512)   # threads per block of the traversal's test and emit passes
 
 
 def secondary_rays(scene, gbuffer: Dict[str, np.ndarray], lights: np.ndarray, n: int, hash_lo, hash_hi,
@@ -57,7 +58,7 @@ class BatchRun:
     """Buffers and calls for one batch of prebuilt rays with a given hierarchy shape."""
 
     def __init__(self, scene, rays: Dict[str, torch.Tensor], n: int, bundle: int, levels: int, pads, hp,
-                 device="cuda"):
+                 device="cuda", block: int = 256):
         self.n = n
         self.rays = rays
         self.p = Pipeline(scene, max_pixels=0, n_lights=0, bundle=bundle, levels=levels, ray_capacity=max(1, n),
@@ -65,13 +66,13 @@ class BatchRun:
         self.rin = Pipeline.rays_in_struct(rays)
         self.hp = hp
         self.bp = build_params(bundle, levels, pads)
-        self.bundle, self.levels = bundle, levels
+        self.bundle, self.levels, self.block = bundle, levels, block
 
     def run(self, stream: int):
         p = self.p
         p.hash_sort(None, None, self.hp, stream, rays_in=self.rin)
         p.build(self.bp, stream)
-        p.traverse(True, stream)
+        p.traverse(True, stream, self.block)
         p.closest_hit(stream)
 
     def fit(self, max_tries=8) -> dict:
@@ -107,35 +108,48 @@ def _time_ms(fn, reps=3) -> float:
 
 
 class Autotuner:
-    """Picks (B, L) per batch-size class (floor(log2 n)) by timing every candidate on a
-    representative batch of that class; results are reused for the other batches of the class."""
+    """Picks (B, L, block) per batch-size class (floor(log2 n)) by timing candidates on a
+    representative batch of that class: every (B, L) at the default block shape, then the
+    block shapes of the traversal passes for the best (B, L).  Results are reused for the
+    other batches of the class."""
 
-    def __init__(self, bundles: Sequence[int] = BUNDLES, depths: Sequence[int] = DEPTHS, reps: int = 3):
-        self.bundles, self.depths, self.reps = tuple(bundles), tuple(depths), reps
-        self.table: Dict[int, Tuple[int, int]] = {}
+    def __init__(self, bundles: Sequence[int] = BUNDLES, depths: Sequence[int] = DEPTHS, reps: int = 3,
+                 blocks: Sequence[int] = BLOCKS):
+        self.bundles, self.depths, self.reps, self.blocks = tuple(bundles), tuple(depths), reps, tuple(blocks)
+        self.table: Dict[int, Tuple[int, int, int]] = {}
         self.log: List[dict] = []
 
     @staticmethod
     def size_class(n: int) -> int:
         return int(math.floor(math.log2(max(1, n))))
 
-    def choose(self, scene, rays, n, pads, hp, device="cuda") -> Tuple[int, int]:
+    def choose(self, scene, rays, n, pads, hp, device="cuda") -> Tuple[int, int, int]:
         k = self.size_class(n)
         if k in self.table:
             return self.table[k]
-        best, best_ms = (16, 4), float("inf")
+        best, best_ms = (16, 4, 256), float("inf")
         stream = lambda: torch.cuda.current_stream().cuda_stream  # noqa: E731
+
+        def trial(B, L, blk):
+            br = BatchRun(scene, rays, n, B, L, pads, hp, device, block=blk)
+            br.fit()
+            ms = _time_ms(lambda: br.run(stream()), self.reps)
+            self.log.append({"size_class": k, "bundle": B, "levels": L, "block": blk, "ms": ms})
+            del br
+            return ms
+        blk0 = 256 if 256 in self.blocks else self.blocks[0]
         for B in self.bundles:
             for L in self.depths:
                 if B ** (L - 1) > max(n, 1):   # more levels than the batch can fill
                     continue
-                br = BatchRun(scene, rays, n, B, L, pads, hp, device)
-                br.fit()
-                ms = _time_ms(lambda: br.run(stream()), self.reps)
-                self.log.append({"size_class": k, "bundle": B, "levels": L, "ms": ms})
+                ms = trial(B, L, blk0)
                 if ms < best_ms:
-                    best, best_ms = (B, L), ms
-                del br
+                    best, best_ms = (B, L, blk0), ms
+        for blk in self.blocks:
+            if blk != blk0:
+                ms = trial(best[0], best[1], blk)
+                if ms < best_ms:
+                    best, best_ms = (best[0], best[1], blk), ms
         torch.cuda.empty_cache()
         self.table[k] = best
         return best
@@ -150,8 +164,8 @@ class BatchedCRSH:
         self.tuner = tuner or Autotuner()
         self.runs: List[BatchRun] = []
         for scene, rays, n in batches:
-            B, L = self.tuner.choose(scene, rays, n, pads_of(scene), hp_of(scene), device)
-            br = BatchRun(scene, rays, n, B, L, pads_of(scene), hp_of(scene), device)
+            B, L, blk = self.tuner.choose(scene, rays, n, pads_of(scene), hp_of(scene), device)
+            br = BatchRun(scene, rays, n, B, L, pads_of(scene), hp_of(scene), device, block=blk)
             br.fit()
             self.runs.append(br)
         self.n_streams = n_streams
@@ -185,16 +199,34 @@ class BatchedCRSH:
 
 
 class PlainBatches:
-    """Reference: each batch through the four calls in turn, default B = 16, L = 4, one stream."""
+    """Reference: each batch through the four calls in turn, default B = 16, L = 4, one stream.
+    capture() records the same calls, in the same order on one stream, as one CUDA graph
+    (the ablation that removes only the host's launch gaps)."""
 
-    def __init__(self, batches, pads_of, hp_of, device="cuda"):
+    def __init__(self, batches, pads_of, hp_of, device="cuda", bundle=16, levels=4):
+        self.device = torch.device(device)
         self.runs = []
         for scene, rays, n in batches:
-            br = BatchRun(scene, rays, n, 16, 4, pads_of(scene), hp_of(scene), device)
+            br = BatchRun(scene, rays, n, bundle, levels, pads_of(scene), hp_of(scene), device)
             br.fit()
             self.runs.append(br)
+        self.graph = None
 
     def run(self):
         stream = torch.cuda.current_stream().cuda_stream
         for r in self.runs:
             r.run(stream)
+
+    def capture(self):
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(self.device)
+        with torch.cuda.graph(g, stream=cap):
+            for r in self.runs:
+                r.run(cap.cuda_stream)
+        self.graph = g
+        self._stream = cap
+        return g
+
+    def replay(self):
+        self.graph.replay()

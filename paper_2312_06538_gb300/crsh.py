@@ -62,7 +62,7 @@ class crsh_hierarchy(ctypes.Structure):
 
 
 class crsh_traverse_params(ctypes.Structure):
-    _fields_ = [("mesh_cull", U32)]
+    _fields_ = [("mesh_cull", U32), ("block_threads", U32)]
 
 
 class crsh_pairs(ctypes.Structure):

@@ -37,7 +37,7 @@ bool rays_ok(const crsh_rays* r) {
 }
 
 bool hier_ok(const crsh_hierarchy* h) {
-    if (!h || !h->count || !pow2_in(h->bundle, 2, 32) || h->levels < 1 || h->levels > CRSH_MAX_LEVELS) return false;
+    if (!h || !h->count || !pow2_in(h->bundle, 2, 64) || h->levels < 1 || h->levels > CRSH_MAX_LEVELS) return false;
     for (unsigned l = 0; l < h->levels; ++l)
         if (!h->sphere[l] || !h->cone[l] || !h->trig[l]) return false;
     return true;
@@ -197,7 +197,7 @@ crsh_status crsh_hash_sort(const crsh_gbuffer* gbuffer, const crsh_rays_in* rays
 crsh_status crsh_build(const crsh_rays* rays, const uint32_t* n_rays, const crsh_build_params* p,
                        crsh_hierarchy* out, void* stream) {
     if (!rays_ok(rays) || !n_rays || !p || !out || !out->count) return CRSH_ERR_INVALID_ARG;
-    if (!pow2_in(p->bundle, 2, 32) || p->levels < 1 || p->levels > CRSH_MAX_LEVELS) return CRSH_ERR_INVALID_ARG;
+    if (!pow2_in(p->bundle, 2, 64) || p->levels < 1 || p->levels > CRSH_MAX_LEVELS) return CRSH_ERR_INVALID_ARG;
     if (!(p->sphere_pad_rel >= 0) || !(p->sphere_pad_abs >= 0) || !(p->cone_pad_rel >= 0) || !(p->cone_pad_abs >= 0))
         return CRSH_ERR_INVALID_ARG;
     uint64_t need = rays->capacity;
@@ -211,7 +211,7 @@ crsh_status crsh_build(const crsh_rays* rays, const uint32_t* n_rays, const crsh
 }
 
 size_t crsh_traverse_workspace(const crsh_hierarchy* h, uint32_t n_tris, uint32_t n_meshes, uint64_t pair_capacity) {
-    if (!h || h->levels < 1 || h->levels > CRSH_MAX_LEVELS || !pow2_in(h->bundle, 2, 32)) return 0;
+    if (!h || h->levels < 1 || h->levels > CRSH_MAX_LEVELS || !pow2_in(h->bundle, 2, 64)) return 0;
     return traverse_workspace(h, n_tris, n_meshes, pair_capacity);
 }
 
@@ -219,6 +219,8 @@ crsh_status crsh_traverse(const crsh_hierarchy* h, const crsh_scene* scene, cons
                           crsh_pairs* out, crsh_counters* counters, void* workspace, size_t workspace_bytes,
                           void* stream) {
     if (!hier_ok(h) || !scene_ok(scene, true) || !p || !out || !counters || !ws_ok(workspace)) return CRSH_ERR_INVALID_ARG;
+    if (p->block_threads != 0 && p->block_threads != 128 && p->block_threads != 256 && p->block_threads != 512)
+        return CRSH_ERR_INVALID_ARG;
     if (!out->node || !out->tri || !out->node_offsets || !out->count || out->capacity == 0 ||
         out->capacity > (1ull << 31))
         return CRSH_ERR_INVALID_ARG;

@@ -117,7 +117,9 @@ __device__ __forceinline__ void pad_node(SC& n, const Pads& p) {
 // Balanced binary tree of merges in item order: at steps s = 1, 2, 4, ...,
 // item i (a multiple of 2s) absorbs item i + s when it exists.  A node's items
 // sit in B consecutive lanes (B a power of two <= 32), so each step is one
-// shuffle-down within the lane group.
+// shuffle-down within the lane group.  (B = 64 spans two warps: each warp
+// runs the steps below 32 and the last step, item 0 absorbing item 32, goes
+// through shared memory in k_build_up.)
 __device__ __forceinline__ SC shfl_down_sc(const SC& v, unsigned s, int width) {
     SC o;
     o.c.x = __shfl_down_sync(FULL, v.c.x, s, width);
@@ -133,8 +135,9 @@ __device__ __forceinline__ SC shfl_down_sc(const SC& v, unsigned s, int width) {
 
 template <bool CONES>
 __device__ __forceinline__ void group_tree_merge(SC& item, unsigned r, unsigned m, unsigned B) {
-    for (unsigned s = 1; s < B; s <<= 1) {
-        const SC other = shfl_down_sc(item, s, (int)B);
+    const unsigned W = B < 32u ? B : 32u;   // steps below the warp width
+    for (unsigned s = 1; s < W; s <<= 1) {
+        const SC other = shfl_down_sc(item, s, (int)W);
         if ((r & (2 * s - 1)) == 0 && r + s < m) {
             sphere_union(item, other);
             if (CONES) cone_union(item, other);
@@ -334,8 +337,9 @@ __global__ void __launch_bounds__(32) k_build_l1(RaysIn rays, const unsigned* n_
         }
         // level 2 (eqs. 5-8): the block's 32 nodes are 32 / B whole groups,
         // merged here as the level-2 pass would merge them after reading the
-        // stored nodes back (the same values, in the same order)
-        if (L >= 2) {
+        // stored nodes back (the same values, in the same order); with B = 64
+        // a group spans two blocks and level 2 is built by k_build_up
+        if (B <= 32 && L >= 2) {
             const unsigned g = j / B, r2 = lane & (B - 1);
             const unsigned m2 = g < cnt2 ? min((unsigned)B, lim - g * B) : 0u;
             group_tree_merge<true>(node, r2, m2, B);
@@ -361,9 +365,10 @@ static void launch_build_l1(const RaysIn& ri, const uint32_t* n_rays, unsigned L
 __global__ void k_build_up(const float4* csph, const float4* ccone, const unsigned* counts, unsigned level_idx,
                            unsigned B, Pads pads, LevelOut out) {
     pdl_wait();
+    __shared__ SC s_half[4];   // B = 64: each group's second-half result (128-thread blocks: 2 groups)
     const unsigned below = counts[level_idx - 1];
     const unsigned cnt = counts[level_idx];
-    const unsigned lane = threadIdx.x & 31, r = lane & (B - 1);
+    const unsigned r = threadIdx.x & (B - 1);   // child slot in the group (groups of B <= 64 threads)
     const unsigned groups_per_block = blockDim.x / B;
     const unsigned gstart = blockIdx.x * groups_per_block + threadIdx.x / B;
     const unsigned gstride = gridDim.x * groups_per_block;
@@ -386,6 +391,17 @@ __global__ void k_build_up(const float4* csph, const float4* ccone, const unsign
             ch.phi = co.w;
         }
         group_tree_merge<true>(ch, r, m, B);   // eqs. 5-8 in child order
+        if (B > 32) {   // the last step: child 0's subtree absorbs child 32's (block-uniform branch)
+            const unsigned gl = threadIdx.x / B;
+            if (r == 32) s_half[gl] = ch;
+            __syncthreads();
+            if (r == 0 && 32 < m) {
+                const SC other = s_half[gl];
+                sphere_union(ch, other);
+                cone_union(ch, other);
+            }
+            __syncthreads();
+        }
         if (r == 0 && node_ok) {
             pad_node(ch, pads);
             store_node(out, j, ch);
@@ -415,10 +431,11 @@ crsh_status build_launch(const crsh_rays* rays, const uint32_t* n_rays, const cr
         case 8: launch_build_l1<8>(ri, n_rays, L, pads, o1, o2, h->count, caps, h->capacity[0], s, dev); break;
         case 16: launch_build_l1<16>(ri, n_rays, L, pads, o1, o2, h->count, caps, h->capacity[0], s, dev); break;
         case 32: launch_build_l1<32>(ri, n_rays, L, pads, o1, o2, h->count, caps, h->capacity[0], s, dev); break;
+        case 64: launch_build_l1<64>(ri, n_rays, L, pads, o1, o2, h->count, caps, h->capacity[0], s, dev); break;
         default: return CRSH_ERR_INVALID_ARG;
     }
-    // levels 3 and up: B-lane groups over the stored nodes below
-    for (unsigned l = 2; l < L; ++l) {
+    // levels 3 and up (2 and up when B = 64): B-lane groups over the stored nodes below
+    for (unsigned l = (B > 32 ? 1u : 2u); l < L; ++l) {
         LevelOut o{reinterpret_cast<float4*>(h->sphere[l]), reinterpret_cast<float4*>(h->cone[l]),
                    reinterpret_cast<float2*>(h->trig[l]), h->capacity[l]};
         const unsigned blocks = (unsigned)(((size_t)h->capacity[l] * B + 127) / 128);

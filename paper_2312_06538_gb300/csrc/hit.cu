@@ -530,6 +530,7 @@ crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, c
         case 8: launch_closest<8>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
         case 16: launch_closest<16>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
         case 32: launch_closest<32>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
+        case 64: launch_closest<64>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
         default: return CRSH_ERR_INVALID_ARG;
     }
     launch_pdl(k_finalize, fb, 256, 0, s, rd, n_rays, cap, *sc, best, *out);

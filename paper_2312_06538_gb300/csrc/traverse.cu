@@ -16,6 +16,7 @@
 // which is how the next level finds a parent's triangles.
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -445,8 +446,8 @@ __device__ __forceinline__ float4 chunk_sphere(float4 ts, bool valid) {
 // bounding sphere: eq. 9 is an exact sphere-against-region test, so a child
 // that rejects the bounding sphere rejects every triangle sphere inside it
 // (its word is 0) and only the children that accept it run the 32-lane tests.
-template <class Parents>
-__global__ void __launch_bounds__(256, 6) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
+template <class Parents, int BLK, bool WIDE>
+__global__ void __launch_bounds__(BLK, 1536 / BLK) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
     pdl_wait();
     const WorkSplit ws(sb.totals[0], sb.work + 0, 16u);
     const int lane = threadIdx.x & 31;
@@ -483,16 +484,21 @@ __global__ void __launch_bounds__(256, 6) k_count(Parents par, StageBuf sb, cons
         unsigned* mw = sb.mask + c0.ob + (p0.u - c0.ub);
         if (Parents::kChunkCull) {
             const float4 K = chunk_sphere(ts0, v0);
-            const bool mine = (unsigned)lane < nc;
-            const bool acc = mine && eq9(csp[lane], cco[lane], ctg[lane], K);
-            if (mine && !acc) mw[lane * nch] = 0u;
-            unsigned todo = __ballot_sync(FULL, acc);
-            while (todo) {
-                const unsigned c = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
-                const unsigned m = __ballot_sync(FULL, ok);
-                if (lane == 0) mw[c * nch] = m;
+            // children in groups of 32 (lane = child); more than one group only when B = 64
+#pragma unroll
+            for (unsigned cb = 0; cb < (WIDE ? 64u : 32u); cb += 32) {
+                const unsigned cl = cb + lane;
+                const bool mine = cl < nc;
+                const bool acc = mine && eq9(csp[cl], cco[cl], ctg[cl], K);
+                if (mine && !acc) mw[cl * nch] = 0u;
+                unsigned todo = __ballot_sync(FULL, acc);
+                while (todo) {
+                    const unsigned c = cb + __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
+                    const unsigned m = __ballot_sync(FULL, ok);
+                    if (lane == 0) mw[c * nch] = m;
+                }
             }
         } else {
 #pragma unroll 4
@@ -624,26 +630,33 @@ __global__ void __launch_bounds__(SC_BLOCK) k_wordscan(StageBuf sb, PairOut out,
 // (child, triangle) pair at pos[word] + rank.  Unit (p, 0) also records the
 // children's runs [start, end).  The triangle index and the children's words
 // of the next unit are loaded while the current unit is written.
-template <class Parents>
+template <class Parents, int G>
 struct EmitLoads {
-    unsigned t, mc, pc, pe;   // triangle; child `lane`'s mask and position; its run end (first chunk)
+    // triangle; per group of 32 children, child `lane`'s mask and position and
+    // its run end (first chunk); G = 2 groups only when B = 64
+    unsigned t, mc[G], pc[G], pe[G];
     __device__ __forceinline__ void load(const Parents& par, const StageBuf& sb, const UnitStream<Parents>& q) {
         const int lane = threadIdx.x & 31;
         bool valid;
         t = q.c.tri(par, q.u, valid);
         const unsigned nch = (q.c.len + 31) >> 5, nc = par.nchild(q.c.p), ch = q.u - q.c.ub;
-        mc = pc = pe = 0;
-        if ((unsigned)lane < nc) {
-            const unsigned w = q.c.ob + lane * nch + ch;
-            mc = sb.mask[w];
-            pc = sb.pos[w];
-            if (ch == 0) pe = sb.pos[q.c.ob + (lane + 1) * nch];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const unsigned cl = 32u * g + lane;
+            mc[g] = pc[g] = pe[g] = 0;
+            if (cl < nc) {
+                const unsigned w = q.c.ob + cl * nch + ch;
+                mc[g] = sb.mask[w];
+                pc[g] = sb.pos[w];
+                if (ch == 0) pe[g] = sb.pos[q.c.ob + (cl + 1) * nch];
+            }
         }
     }
 };
 
-template <class Parents>
-__global__ void __launch_bounds__(256) k_emit(Parents par, StageBuf sb, PairOut out, RunOut runs) {
+template <class Parents, int BLK, bool WIDE>
+__global__ void __launch_bounds__(BLK) k_emit(Parents par, StageBuf sb, PairOut out, RunOut runs) {
+    constexpr int G = WIDE ? 2 : 1;
     pdl_wait();
     const WorkSplit ws(sb.totals[0], sb.work + 1, 32u);
     const int lane = threadIdx.x & 31;
@@ -651,7 +664,7 @@ __global__ void __launch_bounds__(256) k_emit(Parents par, StageBuf sb, PairOut 
     unsigned claim = ws.first_claim();
     UnitStream<Parents> p0;
     if (!p0.take(par, sb, ws, claim)) return;
-    EmitLoads<Parents> l0, l1;
+    EmitLoads<Parents, G> l0, l1;
     l0.load(par, sb, p0);
     UnitStream<Parents> p1 = p0;
     bool has1 = p1.step(par, sb, ws, claim);
@@ -662,20 +675,24 @@ __global__ void __launch_bounds__(256) k_emit(Parents par, StageBuf sb, PairOut 
         if (has1) has2 = p2.step(par, sb, ws, claim);
         const UnitCursor<Parents>& c0 = p0.c;
         const unsigned nc = par.nchild(c0.p), ch = p0.u - c0.ub;
-        unsigned any = __ballot_sync(FULL, l0.mc != 0);
-        while (any) {
-            const int c = __ffs(any) - 1;
-            any &= any - 1;
-            const unsigned m = __shfl_sync(FULL, l0.mc, c);
-            const unsigned base = __shfl_sync(FULL, l0.pc, c);
-            if ((m >> lane) & 1u) store_pair(out, base + __popc(m & lt), par.child_id(c0.p, c), l0.t);
-        }
-        if (ch == 0 && (unsigned)lane < nc) {
-            // runs index the written list: clamp to its capacity (a list
-            // that overflowed is truncated and flagged CRSH_ERR_CAPACITY)
-            const unsigned a = par.child_id(c0.p, lane);
-            if (par.first_of_child(c0.p, lane)) runs.start[a] = (unsigned)min((unsigned long long)l0.pc, out.cap);
-            if (par.last_of_child(c0.p, lane)) runs.end[a] = (unsigned)min((unsigned long long)l0.pe, out.cap);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            unsigned any = __ballot_sync(FULL, l0.mc[g] != 0);
+            while (any) {
+                const int c = __ffs(any) - 1;
+                any &= any - 1;
+                const unsigned m = __shfl_sync(FULL, l0.mc[g], c);
+                const unsigned base = __shfl_sync(FULL, l0.pc[g], c);
+                if ((m >> lane) & 1u) store_pair(out, base + __popc(m & lt), par.child_id(c0.p, 32 * g + c), l0.t);
+            }
+            const unsigned cl = 32u * g + lane;
+            if (ch == 0 && cl < nc) {
+                // runs index the written list: clamp to its capacity (a list
+                // that overflowed is truncated and flagged CRSH_ERR_CAPACITY)
+                const unsigned a = par.child_id(c0.p, cl);
+                if (par.first_of_child(c0.p, cl)) runs.start[a] = (unsigned)min((unsigned long long)l0.pc[g], out.cap);
+                if (par.last_of_child(c0.p, cl)) runs.end[a] = (unsigned)min((unsigned long long)l0.pe[g], out.cap);
+            }
         }
         if (!has1) break;
         p0 = p1;
@@ -824,8 +841,10 @@ static unsigned resident_blocks(K kernel, int block, const DeviceInfo& dev) {
     return (unsigned)b;
 }
 
-// stage: 0 = top level, then 1, 2, ... for levels L-1, L-2, ...
-template <class Parents>
+// stage: 0 = top level, then 1, 2, ... for levels L-1, L-2, ...  BLK: threads
+// per block of the count and emit passes (a tuning knob: the passes claim
+// their work from counters, so results do not depend on it).
+template <int BLK, bool WIDE, class Parents>
 static void run_stage(const Parents& par, const TvWs& w, unsigned stage, const float4* tsph, PairOut out,
                       RunOut runs, crsh_counters* ctr, int level_idx, unsigned B_paper, const DeviceInfo& dev,
                       cudaStream_t s) {
@@ -833,13 +852,13 @@ static void run_stage(const Parents& par, const TvWs& w, unsigned stage, const f
     sb.work = w.work + 2 * stage;
     const unsigned sg = std::min<unsigned>(SC_GRID_MAX, dev.sms * 8);
     // persistent grids: the count and emit passes claim unit batches
-    const unsigned gc = dev.sms * resident_blocks(k_count<Parents>, 256, dev);
-    const unsigned ge = dev.sms * resident_blocks(k_emit<Parents>, 256, dev);
+    const unsigned gc = dev.sms * resident_blocks(k_count<Parents, BLK, WIDE>, BLK, dev);
+    const unsigned ge = dev.sms * resident_blocks(k_emit<Parents, BLK, WIDE>, BLK, dev);
     launch_pdl(k_unit_scan<Parents>, 1, 1024, 0, s, par, sb, ctr, level_idx, B_paper);
-    launch_pdl(k_count<Parents>, gc, 256, 0, s, par, sb, tsph);
+    launch_pdl(k_count<Parents, BLK, WIDE>, gc, BLK, 0, s, par, sb, tsph);
     launch_pdl(k_reduce, sg, SC_BLOCK, 0, s, sb);
     launch_pdl(k_wordscan, sg, SC_BLOCK, 0, s, sb, out, ctr, level_idx);
-    launch_pdl(k_emit<Parents>, ge, 256, 0, s, par, sb, out, runs);
+    launch_pdl(k_emit<Parents, BLK, WIDE>, ge, BLK, 0, s, par, sb, out, runs);
 }
 
 crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const crsh_traverse_params* tp,
@@ -872,7 +891,17 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     launch_pdl(k_compact<MeshOp>, dev.sms * 2, TV_BLOCK, 0, s, mop, TvCtl{w.st_mesh, &w.tile_ctr[0], ctr, -1});
     // top level: triangles of the accepted meshes
     TopParents top{w.mpN, w.mpM, &w.counts[0], sc->mesh_first_tri, level_nodes(L)};
-    run_stage(top, w, 0u, tsph, pairs_of(L), w.runs[L - 1], ctr, (int)L - 1, 0u, dev, s);
+    // the block shape, and for the level stages whether a parent has more
+    // than 32 children (B = 64); the top stage has one child per parent
+    auto stage = [&](const auto& par, unsigned st, PairOut o, RunOut rn, int li, unsigned Bp, auto wide) {
+        constexpr bool W = decltype(wide)::value;
+        switch (tp->block_threads) {
+            case 128: run_stage<128, W>(par, w, st, tsph, o, rn, ctr, li, Bp, dev, s); break;
+            case 512: run_stage<512, W>(par, w, st, tsph, o, rn, ctr, li, Bp, dev, s); break;
+            default: run_stage<256, W>(par, w, st, tsph, o, rn, ctr, li, Bp, dev, s); break;
+        }
+    };
+    stage(top, 0u, pairs_of(L), w.runs[L - 1], (int)L - 1, 0u, std::false_type{});
     {
         const PairOut tp_out = pairs_of(L);
         launch_pdl(k_runs_from_pairs, dev.sms * 4, 256, 0, s, tp_out.node, tp_out.count, w.runs[L - 1]);
@@ -881,7 +910,10 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     for (unsigned l = L - 1; l >= 1; --l) {
         PairOut par = pairs_of(l + 1);
         LevelParents lp{par.tri, w.runs[l].start, w.runs[l].end, h->count + l, h->count + (l - 1), level_nodes(l), logB};
-        run_stage(lp, w, L - l, tsph, pairs_of(l), w.runs[l - 1], ctr, (int)l - 1, B, dev, s);
+        if (B > 32)
+            stage(lp, L - l, pairs_of(l), w.runs[l - 1], (int)l - 1, B, std::true_type{});
+        else
+            stage(lp, L - l, pairs_of(l), w.runs[l - 1], (int)l - 1, B, std::false_type{});
         if (l == 1) break;
     }
     {

@@ -159,9 +159,9 @@ class Pipeline:
     def build(self, bp: C.crsh_build_params, stream: int):
         C.crsh_build(self.rays, _ptr(self.n_rays), bp, self.hier, stream)
 
-    def traverse(self, mesh_cull: bool, stream: int):
-        C.crsh_traverse(self.hier, self.scene, C.crsh_traverse_params(int(bool(mesh_cull))), self.pairs,
-                        _ptr(self.counters), _ptr(self.ws_trav), self.ws_trav_bytes, stream)
+    def traverse(self, mesh_cull: bool, stream: int, block_threads: int = 0):
+        C.crsh_traverse(self.hier, self.scene, C.crsh_traverse_params(int(bool(mesh_cull)), int(block_threads)),
+                        self.pairs, _ptr(self.counters), _ptr(self.ws_trav), self.ws_trav_bytes, stream)
 
     def closest_hit(self, stream: int):
         C.crsh_closest_hit(self.hier, self.rays, _ptr(self.n_rays), self.scene, self.pairs, self.hits,

@@ -49,7 +49,8 @@ def test_batched_graph_equals_plain_bitwise():
             for x, y in zip(a.hits(), b.hits()):
                 assert torch.equal(x.view(torch.int32), y.view(torch.int32))
     assert set(tuner.table) == {bt.Autotuner.size_class(n) for n, _ in spec}
-    assert all((b, l) in [(8, 2), (8, 4), (16, 2), (16, 4)] for b, l in tuner.table.values())
+    assert all((b, l) in [(8, 2), (8, 4), (16, 2), (16, 4)] and blk in (128, 256, 512)
+               for b, l, blk in tuner.table.values())
     assert sum(int((r.hits()[0] >= 0).sum().item()) for r in bat.runs) > 1000
 
 

@@ -167,7 +167,7 @@ def test_unsorted_uncompressed_and_no_mesh_cull_modes():
     assert np.array_equal(p.hits_host()[0], p2.hits_host()[0])
 
 
-@pytest.mark.parametrize("B,L", [(2, 3), (4, 2), (8, 5), (32, 2), (16, 1)])
+@pytest.mark.parametrize("B,L", [(2, 3), (4, 2), (8, 5), (32, 2), (16, 1), (64, 2), (64, 3), (4, 6)])
 def test_bundle_and_depth(B, L):
     import dataclasses
     w = dataclasses.replace(synthetic.make(2, res=64), bundle=B, levels=L)
