@@ -507,8 +507,8 @@ def hbm_sweep(args, tiles_list=(1, 2, 4, 8, 16, 22), reps: int = 20):
     """Hash+sort (one crsh_hash_sort call: generation, hashing, trimming, compression, 4-pass
     radix sort, decompression + gather) and build (crsh_build) at 3M..70M rays: G-buffers of
     1..22 perturbed tiles of the 1024x1024 frame of config 3.  Algorithmic bytes per call:
-    hash 41 B per pixel read + 41 B per ray written, sort 16 B per sorted chunk (one read and
-    one write of key and value), decompress + gather 4 + 33 + 41 B per ray; build 28 B per ray
+    hash 40 B per pixel read + 41 B per ray written, sort 16 B per sorted chunk (one read and
+    one write of key and value), decompress + gather 4 + 28 + 28 B per ray; build 28 B per ray
     read + 40 B per level-1 node written.  Median of reps, L2 flushed before each."""
     import synthetic
     import torch
@@ -549,7 +549,10 @@ def hbm_sweep(args, tiles_list=(1, 2, 4, 8, 16, 22), reps: int = 20):
             return statistics.median(ts)
         t_hash = med(lambda: p.hash_sort(gs, lights, hp, sh))
         t_build = med(lambda: p.build(bp, sh))
-        b_hash = 41 * npx + 41 * n + 16 * chunks + (4 + 33 + 41) * n
+        # the algorithmic bytes of the method's steps: hash 40 B per pixel read (the G-buffer's
+        # position, normal, incident direction and material) + 41 B per ray written; sort 16 B per
+        # sorted element; decompression + gather 4 B (permutation) + 28 B read + 28 B written per ray
+        b_hash = 40 * npx + 41 * n + 16 * chunks + (4 + 28 + 28) * n
         b_build = 28 * n + 40 * ((n + w.bundle - 1) // w.bundle)
         line = {"sweep": "hash_sort+build HBM", "pixels": npx, "rays": n, "chunks": chunks,
                 "hash_sort_ms": t_hash, "hash_sort_gbs": b_hash / (t_hash * 1e-3) / 1e9,
@@ -692,10 +695,12 @@ def run_gpu(args, w):
     c = p.run_fit(gstruct, lights, hp, bp)          # sizes the pair lists, checks the status
     n_rays = c["rays"]
     if args.profile_steps:
-        # for profilers: the path's calls issued directly, nothing timed or printed
+        # for profilers: the path's calls issued directly, nothing timed; prints the counters
         for _ in range(args.profile_steps):
             p.run(gstruct, lights, hp, bp)
         torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_steps": args.profile_steps, "workload": workload_description(w),
+                          "pixels": w.n_pixels, "counters": {k: v for k, v in c.items()}}), flush=True)
         return
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -822,6 +827,14 @@ def run_gpu(args, w):
                                        f"(max SM clock, {peak_src} peaks file)",
                 "algorithmic": f"{MT_FLOPS} FP32 flops (one Moller-Trumbore test) per candidate ray-triangle test x "
                                f"{c['final_tests']} candidate tests per launch"}
+    # the traversal stage (its count, scan and emit kernels; k_count is its top kernel) against the
+    # same FP32 peak: eq. 9 work of the tests the paper's count makes, per call
+    roofline_traverse = {"kernel": "crsh_traverse (k_count + k_emit + scans, all levels)", "bound": "alu",
+                         "achieved": eq9_tests * EQ9_FLOPS / (tr_ms * 1e-3) / 1e12, "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": eq9_tests * EQ9_FLOPS / (tr_ms * 1e-3) / 1e12 / peak_tf,
+                         "traffic": None,
+                         "algorithmic": f"{EQ9_FLOPS} FP32 flops per eq. 9 test x {eq9_tests} tests per call "
+                                        f"(every child x parent triangle, mesh tests included)"}
     total_tests = c["final_tests"] + eq9_tests
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -846,6 +859,7 @@ def run_gpu(args, w):
         "traverse_eq9_tflops": eq9_tests * EQ9_FLOPS / (tr_ms * 1e-3) / 1e12,
         "wall_ms_timed_region": 1e3 * t_wall,
         "roofline": roofline,
+        "roofline_traverse": roofline_traverse,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step(w.levels, True) * args.steps,
         "clocks": clocks,
