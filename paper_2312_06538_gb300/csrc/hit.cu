@@ -125,7 +125,17 @@ __device__ __forceinline__ void prefetch_node_rays(const RaysDev& rays, unsigned
     prefetch_l1(rays.tmax + i);
 }
 
-constexpr unsigned CH_PAIRS = 96;   // pairs per work chunk: three full groups (measured best of 64, 80, 96, 128, 256)
+// Pairs per work chunk: a multiple of the 32-pair group, about CH_CLAIMS
+// claims per warp, between CH_MIN and CH_MAX.  Larger chunks cost fewer
+// claims and node changes per pair; smaller ones balance the end of the
+// launch (fixed sizes: on the 512x512 frame 96 pairs measured best of 64 to
+// 256, on the 1024x1024 frame 256; of 16, 32, 48, 64 and 96 claims per warp,
+// 32 measured best there, 1.95 ms).
+constexpr unsigned CH_MIN = 96, CH_MAX = 512, CH_CLAIMS = 32;
+__device__ __forceinline__ unsigned chunk_pairs(unsigned P) {
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    return max(CH_MIN, min(CH_MAX, (P / (nw * CH_CLAIMS)) & ~31u));
+}
 
 // min over the lanes that hold the same ray (one per stream), then one
 // atomicMin per ray
@@ -140,7 +150,7 @@ __device__ __forceinline__ void flush_best(unsigned long long bk, bool rvalid, i
     if (rvalid && sidx == 0 && bk != NO_HIT) atomicMin(&best[ray], bk);
 }
 
-// Warps take chunks of CH_PAIRS consecutive pairs of the node-sorted pair
+// Warps take chunks of chunk_pairs(P) consecutive pairs of the node-sorted pair
 // list from an atomic counter (the cost of a chunk depends on how many nodes
 // it spans) and walk them in groups: up to 32 consecutive pairs of one node.
 // Each lane holds two rays of the node (slots r and r + B/2) as a RayPair;
@@ -168,6 +178,7 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest(const uint32_t* pnode, 
     __shared__ unsigned s_tid[CH_WARPS][2][32];
     const unsigned P = (unsigned)min((unsigned long long)*p_count, p_cap);
     const unsigned N = min(*n_ptr, n_cap);   // rays past the capacity are never touched
+    const unsigned CH_PAIRS = chunk_pairs(P);
     const unsigned n_chunks = (P + CH_PAIRS - 1) / CH_PAIRS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = lane % H, sidx = lane / H;

@@ -356,20 +356,22 @@ struct UnitCursor {
 // Work split of a count or emit pass.  With at least dyn_min units per warp
 // the units are handed out in batches from an atomic counter (the cost of a
 // unit depends on how many children accept it), about four batches per warp
-// and at most UNIT_BATCH units each; a warp claims the batch after the
+// and at most COUNT_BATCH / EMIT_BATCH units each; a warp claims the batch after the
 // current one when it starts a batch, so the claim's latency is hidden.  With
 // fewer, each warp takes one contiguous range (no atomics: at a few units per
 // warp the claims themselves would dominate).  The position (cursor, unit u,
 // batch end e) advances one unit at a time.  All calls are warp-uniform.
-constexpr unsigned UNIT_BATCH = 8;   // of 4, 6, 8, 16, 32: 8 measured best (traversal 404 us against 413 at 16)
+constexpr unsigned COUNT_BATCH = 16;  // units per claim of the count pass (of 8, 16, 32: 16 measured best on the 1024x1024 frame)
+constexpr unsigned EMIT_BATCH = 16;   // units per claim of the emit pass (of 8, 16, 32: 16 measured best on the 1024x1024 frame)
 
 struct WorkSplit {
     unsigned U, nw, per, batch;   // per = 0: claimed batches; else the static range length
     unsigned* work;
-    __device__ __forceinline__ WorkSplit(unsigned U_, unsigned* work_, unsigned dyn_min) : U(U_), work(work_) {
+    __device__ __forceinline__ WorkSplit(unsigned U_, unsigned* work_, unsigned dyn_min, unsigned max_batch)
+        : U(U_), work(work_) {
         nw = gridDim.x * (blockDim.x >> 5);
         per = (U >= dyn_min * nw) ? 0u : (U + nw - 1) / nw;
-        batch = max(1u, min(UNIT_BATCH, U / (4u * nw)));
+        batch = max(1u, min(max_batch, U / (4u * nw)));
     }
     // first claim: the warp's own index for a static split
     __device__ __forceinline__ unsigned first_claim() const {
@@ -449,7 +451,7 @@ __device__ __forceinline__ float4 chunk_sphere(float4 ts, bool valid) {
 template <class Parents, int BLK, bool WIDE>
 __global__ void __launch_bounds__(BLK, 1536 / BLK) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
     pdl_wait();
-    const WorkSplit ws(sb.totals[0], sb.work + 0, 16u);
+    const WorkSplit ws(sb.totals[0], sb.work + 0, 16u, COUNT_BATCH);
     const int lane = threadIdx.x & 31;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned claim = ws.first_claim();
@@ -658,7 +660,7 @@ template <class Parents, int BLK, bool WIDE>
 __global__ void __launch_bounds__(BLK) k_emit(Parents par, StageBuf sb, PairOut out, RunOut runs) {
     constexpr int G = WIDE ? 2 : 1;
     pdl_wait();
-    const WorkSplit ws(sb.totals[0], sb.work + 1, 32u);
+    const WorkSplit ws(sb.totals[0], sb.work + 1, 32u, EMIT_BATCH);
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     unsigned claim = ws.first_claim();
