@@ -117,14 +117,6 @@ __device__ __forceinline__ float ray_kid2(float dx, float dy, float dz) {
     return __fdiv_rn(PRETEST_K1, __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
 }
 
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-
-__device__ __forceinline__ void prefetch_node_rays(const RaysDev& rays, unsigned i) {
-    prefetch_l1(rays.ox + i); prefetch_l1(rays.oy + i); prefetch_l1(rays.oz + i);
-    prefetch_l1(rays.dx + i); prefetch_l1(rays.dy + i); prefetch_l1(rays.dz + i);
-    prefetch_l1(rays.tmax + i);
-}
-
 // Pairs per work chunk: a multiple of the 32-pair group, about CH_CLAIMS
 // claims per warp, between CH_MIN and CH_MAX.  Larger chunks cost fewer
 // claims and node changes per pair; smaller ones balance the end of the
@@ -266,10 +258,6 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest(const uint32_t* pnode, 
                 stage(buf ^ 1, ncnt, pt1);
                 has2 = advance(q1, e1, ncnt);
                 if (has2) window(q1, e1, pw2, pt2);
-                if (nnode != cur) {   // warm L1 with the next node's rays
-                    const unsigned nr = nnode * B + r;
-                    if (nr < N) prefetch_node_rays(rays, nr);
-                }
             } else {
                 cp_async_commit();   // keeps "all but the newest group" meaning this group
             }
@@ -312,13 +300,6 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest(const uint32_t* pnode, 
                 }
             }
             __syncwarp();   // buffer buf is refilled two groups on
-            if (has2) {   // warm L1 with the rays of every node that starts in the window two groups on
-                const unsigned prev = __shfl_up_sync(FULL, pw2, 1);
-                if (pw2 != 0xffffffffu && (lane == 0 || prev != pw2)) {
-                    const unsigned nr = pw2 * B;   // the node's B rays share one 64-byte-aligned span per array
-                    if (nr < N) prefetch_node_rays(rays, nr);
-                }
-            }
             if (!has1) break;
             if (nnode != cur) {
                 flush_best<H>(k0, v0, sidx, ray0, best);
