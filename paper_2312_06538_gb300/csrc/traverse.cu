@@ -125,9 +125,12 @@ __global__ void __launch_bounds__(TV_BLOCK) k_compact(Op op, TvCtl ctl) {
     }
 }
 
+// o.node == nullptr: a list whose node column nobody reads (the levels
+// between the top and level 1: the next level finds a node's triangles by
+// its run), so only the triangle column is written
 __device__ __forceinline__ void store_pair(const PairOut& o, unsigned long long pos, uint32_t a, uint32_t b) {
     if (pos < o.cap) {
-        o.node[pos] = a;
+        if (o.node) o.node[pos] = a;
         o.tri[pos] = b;
     }
 }
@@ -882,9 +885,11 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
                      reinterpret_cast<const float2*>(h->trig[l - 1])};
     };
     const float4* tsph = reinterpret_cast<const float4*>(sc->tri_sphere);
+    // the top level's node column feeds k_runs_from_pairs and level 1's is the
+    // output; the levels between keep only triangles (their runs locate them)
     auto pairs_of = [&](unsigned l) {
         if (l == 1) return PairOut{out->node, out->tri, out->count, cap};
-        return PairOut{w.bufN[l & 1], w.bufT[l & 1], &w.counts[1 + l], cap};
+        return PairOut{l == L ? w.bufN[l & 1] : nullptr, w.bufT[l & 1], &w.counts[1 + l], cap};
     };
     // mesh stage: (top node, mesh)
     MeshOp mop{level_nodes(L), h->count + (L - 1), reinterpret_cast<const float4*>(sc->mesh_sphere),
