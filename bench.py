@@ -303,7 +303,7 @@ def launches_per_step(levels: int, compress: bool) -> int:
     # tables, gen, chunk (which also counts the digits) or hist, plan, 4 passes, pos, gather
     hash_sort = 1 + 1 + 1 + 1 + 4 + (1 if compress else 0) + 1
     build = max(1, levels - 1)   # level 1 (with level 2 merged in), then one per level above
-    traverse = 1 + 5 + 1 + 5 * (levels - 1) + 1   # mesh stage, top stage + its runs, 5 kernels per level, csr
+    traverse = 1 + 5 + 5 * (levels - 1) + 1   # mesh stage, top stage, 5 kernels per level, csr
     closest = 3
     return hash_sort + build + traverse + closest
 

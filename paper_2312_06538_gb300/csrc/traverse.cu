@@ -227,10 +227,12 @@ struct TopParents {             // parents: accepted (top node, mesh) pairs, gro
     __device__ unsigned nchild(unsigned) const { return 1u; }
     __device__ unsigned child_id(unsigned i, unsigned) const { return mp_node[i]; }
     __device__ unsigned tri(unsigned s, unsigned j) const { return s + j; }
-    // a top node's pairs span several mesh pairs: its run is found afterwards
-    // by k_runs_from_pairs
-    __device__ bool first_of_child(unsigned, unsigned) const { return false; }
-    __device__ bool last_of_child(unsigned, unsigned) const { return false; }
+    // a top node's pairs span its accepted meshes' runs (parents are grouped by
+    // node): its first mesh parent records the run's start, its last the end
+    __device__ bool first_of_child(unsigned i, unsigned) const { return i == 0 || mp_node[i - 1] != mp_node[i]; }
+    __device__ bool last_of_child(unsigned i, unsigned) const {
+        return i + 1 == *a_count || mp_node[i + 1] != mp_node[i];
+    }
 };
 
 struct StageBuf {
@@ -707,18 +709,6 @@ __global__ void __launch_bounds__(BLK) k_emit(Parents par, StageBuf sb, PairOut 
     }
 }
 
-// Runs of a node-sorted pair list: the pair that opens a node's run writes its
-// start, the pair that closes it writes its end (nodes without pairs keep 0, 0).
-__global__ void k_runs_from_pairs(const uint32_t* node, const unsigned* p_count, RunOut runs) {
-    pdl_wait();
-    const unsigned P = *p_count;
-    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
-        const uint32_t n = node[q];
-        if (q == 0 || node[q - 1] != n) runs.start[n] = q;
-        if (q + 1 == P || node[q + 1] != n) runs.end[n] = q + 1;
-    }
-}
-
 // CSR offsets (n + 1) of the node-sorted level-1 list: a node's offset is the
 // start of its run; a node without pairs takes the start of the next node
 // with pairs (the list end if none).  A few steps forward over the runs find
@@ -768,7 +758,7 @@ struct Carve {
 };
 
 struct TvWs {
-    uint32_t *bufN[2], *bufT[2];         // ping-pong pair lists of the levels above 1
+    uint32_t* bufT[2];                   // ping-pong pair lists (triangles) of the levels above 1
     uint32_t *mpN, *mpM;                 // accepted (node, mesh)
     RunOut runs[CRSH_MAX_LEVELS];        // pair runs per level
     StageBuf sb;
@@ -788,10 +778,7 @@ TvWs carve_tv(void* ws, const crsh_hierarchy* h, uint32_t n_tris, uint32_t n_mes
     const uint64_t top_cap = h->capacity[L - 1];
     const size_t mp = (size_t)top_cap * (n_meshes ? n_meshes : 1);
     if (L > 1) {
-        for (int k = 0; k < 2; ++k) {
-            w.bufN[k] = c.take<uint32_t>(cap);
-            w.bufT[k] = c.take<uint32_t>(cap);
-        }
+        for (int k = 0; k < 2; ++k) w.bufT[k] = c.take<uint32_t>(cap);
     }
     w.mpN = c.take<uint32_t>(mp);
     w.mpM = c.take<uint32_t>(mp);
@@ -885,11 +872,11 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
                      reinterpret_cast<const float2*>(h->trig[l - 1])};
     };
     const float4* tsph = reinterpret_cast<const float4*>(sc->tri_sphere);
-    // the top level's node column feeds k_runs_from_pairs and level 1's is the
-    // output; the levels between keep only triangles (their runs locate them)
+    // level 1's node column is the output; the levels above keep only
+    // triangles (the next level finds a node's triangles by its run)
     auto pairs_of = [&](unsigned l) {
         if (l == 1) return PairOut{out->node, out->tri, out->count, cap};
-        return PairOut{l == L ? w.bufN[l & 1] : nullptr, w.bufT[l & 1], &w.counts[1 + l], cap};
+        return PairOut{nullptr, w.bufT[l & 1], &w.counts[1 + l], cap};
     };
     // mesh stage: (top node, mesh)
     MeshOp mop{level_nodes(L), h->count + (L - 1), reinterpret_cast<const float4*>(sc->mesh_sphere),
@@ -909,10 +896,6 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
         }
     };
     stage(top, 0u, pairs_of(L), w.runs[L - 1], (int)L - 1, 0u, std::false_type{});
-    {
-        const PairOut tp_out = pairs_of(L);
-        launch_pdl(k_runs_from_pairs, dev.sms * 4, 256, 0, s, tp_out.node, tp_out.count, w.runs[L - 1]);
-    }
     // levels L-1 .. 1: parents are the nodes of level l+1 and their pair runs
     for (unsigned l = L - 1; l >= 1; --l) {
         PairOut par = pairs_of(l + 1);
