@@ -671,9 +671,13 @@ def study(args):
 
 
 def run_gpu(args, w):
+    import ctypes
+
     import torch
     import torch.distributed as dist
 
+    from paper_2312_06538_gb300 import crsh as C
+    from paper_2312_06538_gb300 import frames as fr
     from paper_2312_06538_gb300 import pipeline as pl
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -765,45 +769,29 @@ def run_gpu(args, w):
     tot_ms, tot_units = reduce_over_ranks(local_ms, float(n_rays) * args.steps, world)
     value = tot_units / (tot_ms * 1e-3) / 1e6
 
-    # end to end through the API with host buffers: pinned G-buffer and lights in (one copy of a
-    # packed staging buffer, each field 256-byte aligned), hits out
-    hits_host = {k: torch.empty(p.ray_capacity, dtype=t.dtype).pin_memory()
-                 for k, t in (("tri", p.hit_tri), ("t", p.hit_t), ("u", p.hit_u), ("v", p.hit_v))}
-    n_host = torch.empty(1, dtype=torch.int32).pin_memory()
+    # end to end through the API with host buffers: every frame's G-buffer and lights go up from one
+    # pinned staging buffer and its hits come back to pinned host memory, two frames in flight
+    # (frames.FrameStream: one frame's copies overlap the other's kernels).  The wall clock spans
+    # the first upload to the last read-back; the L2 flush runs before each frame, inside it.
     fields = dict(g_host)
     fields["lights"] = torch.from_numpy(np.ascontiguousarray(w.lights, np.float32))
-    spans, off = {}, 0
-    for kk, v in fields.items():
-        nb = int(v.numel() * v.element_size())
-        spans[kk] = (off, nb)
-        off = (off + nb + 255) & ~255
-    stage_host = torch.empty(off, dtype=torch.uint8).pin_memory()
-    stage_dev = torch.empty(off, dtype=torch.uint8, device=dev)
-    e2e_dev = {}
-    for kk, v in fields.items():
-        o, nb = spans[kk]
-        stage_host[o:o + nb].copy_(v.reshape(-1).view(torch.uint8))
-        e2e_dev[kk] = stage_dev[o:o + nb].view(v.dtype).view(v.shape)
-    e2e_lights = e2e_dev.pop("lights")
-    e2e_gstruct = p.gbuffer_struct(e2e_dev)
-    h2d = off
-    e2e_times = []
-    for k in range(args.warmup + args.steps):
-        flush.fill_(k & 0xff)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        stage_dev.copy_(stage_host, non_blocking=True)
-        p.run(e2e_gstruct, e2e_lights, hp, bp, stream=sh)
-        n_host.copy_(p.n_rays, non_blocking=True)
-        torch.cuda.synchronize(dev)
-        n = int(n_host.item())
-        for kk, src in (("tri", p.hit_tri), ("t", p.hit_t), ("u", p.hit_u), ("v", p.hit_v)):
-            hits_host[kk][:n].copy_(src[:n], non_blocking=True)
-        torch.cuda.synchronize(dev)
-        if k >= args.warmup:
-            e2e_times.append(time.perf_counter() - t0)
-    d2h = 4 + 16 * n_rays
-    e2e_local_ms = 1e3 * sum(e2e_times)
+    layout = fr.HostLayout(fields)
+    stage_host = layout.pack(fields, layout.host_buffer())
+    fs = fr.FrameStream(p, layout, hp, bp, stream=stream, before_frame=lambda: flush.fill_(3))
+    h2d = layout.nbytes
+    for k in range(args.warmup):
+        fs.push(stage_host)
+    last = fs.drain()
+    assert last.n == n_rays
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        fs.push(stage_host)
+    last = fs.drain()
+    torch.cuda.synchronize(dev)
+    e2e_local_ms = 1e3 * (time.perf_counter() - t0)
+    assert last.n == n_rays and torch.equal(last.tri, p.hit_tri[:n_rays].cpu())
+    d2h = ctypes.sizeof(C.crsh_counters) + 16 * n_rays
     e2e_ms, e2e_units = reduce_over_ranks(e2e_local_ms, float(n_rays) * args.steps, world)
     e2e_value = e2e_units / (e2e_ms * 1e-3) / 1e6
 

@@ -163,9 +163,11 @@ class Pipeline:
         C.crsh_traverse(self.hier, self.scene, C.crsh_traverse_params(int(bool(mesh_cull)), int(block_threads)),
                         self.pairs, _ptr(self.counters), _ptr(self.ws_trav), self.ws_trav_bytes, stream)
 
-    def closest_hit(self, stream: int):
-        C.crsh_closest_hit(self.hier, self.rays, _ptr(self.n_rays), self.scene, self.pairs, self.hits,
-                           _ptr(self.counters), _ptr(self.ws_hit), self.ws_hit_bytes, stream)
+    def closest_hit(self, stream: int, hits: Optional[C.crsh_hits] = None):
+        """Closest hits into `hits` (default: the pipeline's own hit arrays)."""
+        C.crsh_closest_hit(self.hier, self.rays, _ptr(self.n_rays), self.scene, self.pairs,
+                           self.hits if hits is None else hits, _ptr(self.counters), _ptr(self.ws_hit),
+                           self.ws_hit_bytes, stream)
 
     def bruteforce(self, stream: Optional[int] = None):
         stream = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
@@ -190,13 +192,14 @@ class Pipeline:
         return g_verts, g_orig, g_dir
 
     def run(self, gbuf: C.crsh_gbuffer, lights: Optional[torch.Tensor], hp: C.crsh_hash_params,
-            bp: C.crsh_build_params, mesh_cull: bool = True, stream: Optional[int] = None):
-        """One pass of the whole path (asynchronous)."""
+            bp: C.crsh_build_params, mesh_cull: bool = True, stream: Optional[int] = None,
+            hits: Optional[C.crsh_hits] = None):
+        """One pass of the whole path (asynchronous); hits as in closest_hit()."""
         stream = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
         self.hash_sort(gbuf, lights, hp, stream)
         self.build(bp, stream)
         self.traverse(mesh_cull, stream)
-        self.closest_hit(stream)
+        self.closest_hit(stream, hits)
 
     def run_fit(self, gbuf, lights, hp, bp, mesh_cull=True, max_tries=8):
         """run(), growing the pair lists until no level overflows (synchronises)."""
