@@ -87,19 +87,24 @@ __device__ __forceinline__ bool near_line(float ox, float oy, float oz, float dx
 
 // The same pre-test for two rays at once (Blackwell's paired FP32 operations,
 // one instruction for both lanes of a float2): rays in the .x and .y lanes of
-// (-o, d, kid2), the triangle's centre and q repeated in both lanes.
+// (-o, d, kid2), the triangle's centre and q repeated in both lanes.  Each lane
+// computes the scalar test's FP32 operations in the same order and returns the
+// margin rhs - vv, whose sign bit is clear exactly when vv <= rhs for finite
+// operands (an exact tie gives +0; a negative difference never rounds to -0),
+// so the sign bits carry the scalar test's decisions.  A missing ray (kid2
+// NaN) gives a NaN whose sign is not specified: it may pass, and
+// Moller-Trumbore then rejects it (its t_max is 0).
 struct RayPair {
     float2 nox, noy, noz, dx, dy, dz, kid2;
 };
-__device__ __forceinline__ void near_line2(const RayPair& p, float4 cxy, float4 czq, bool& h0, bool& h1) {
+__device__ __forceinline__ float2 near_line2_margin(const RayPair& p, float4 cxy, float4 czq) {
     const float2 vx = __fadd2_rn(make_float2(cxy.x, cxy.y), p.nox);
     const float2 vy = __fadd2_rn(make_float2(cxy.z, cxy.w), p.noy);
     const float2 vz = __fadd2_rn(make_float2(czq.x, czq.y), p.noz);
     const float2 vv = __ffma2_rn(vz, vz, __ffma2_rn(vy, vy, __fmul2_rn(vx, vx)));
     const float2 sd = __ffma2_rn(vz, p.dz, __ffma2_rn(vy, p.dy, __fmul2_rn(vx, p.dx)));
     const float2 rhs = __ffma2_rn(__fmul2_rn(sd, sd), p.kid2, make_float2(czq.z, czq.w));
-    h0 = vv.x <= rhs.x;
-    h1 = vv.y <= rhs.y;
+    return __fadd2_rn(rhs, make_float2(-vv.x, -vv.y));
 }
 
 constexpr unsigned long long NO_HIT = ~0ull;
@@ -207,6 +212,10 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest(const uint32_t* pnode, 
                 cp_async16(&s_tri[warp][b][lane][2], m + 2);
                 cp_async16(&s_tri[warp][b][lane][3], m + 3);
                 s_tid[warp][b][lane] = pt;
+            } else {
+                // past the group: a sphere no line passes through (q = -inf makes the pre-test's
+                // right side -inf, so its margin is negative)
+                s_tri[warp][b][lane][3] = make_float4(0.f, 0.f, 0.f, __int_as_float(0xff800000));
             }
             cp_async_commit();
         };
@@ -265,25 +274,37 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest(const uint32_t* pnode, 
             __syncwarp();
             const unsigned nrays = min((unsigned)B, N - cur * B);
             if (lane == 0) n_tests += (unsigned long long)cnt * nrays;
-            // pre-test every (ray, triangle) of the lane; bit k = triangle sidx + S k
-            unsigned m0 = 0, m1 = 0;
+            // pre-test every (ray, triangle) of the lane: row k is triangle sidx + S k; the
+            // margins' sign bits (miss flags) are shifted in, so after the loop bit kmax - 1 - k
+            // is row k's, and the hit masks are their complements.  Rows past the group's
+            // triangles are skipped; slots past it in the last row hold a sphere that fails.
+            constexpr int K = 32 / S;
+            const unsigned kmax = (cnt + S - 1) / S;   // warp-uniform: rows of the group that hold triangles
+            unsigned x0 = 0, x1 = 0;
+            auto row = [&](int k) {
+                const float4 c = s_tri[warp][buf][sidx + S * k][3];
+                const float2 d = near_line2_margin(rp, make_float4(c.x, c.x, c.y, c.y), make_float4(c.z, c.z, c.w, c.w));
+                x0 = __funnelshift_l(__float_as_uint(d.x), x0, 1);
+                x1 = __funnelshift_l(__float_as_uint(d.y), x1, 1);
+            };
+            if (kmax == (unsigned)K) {   // a full group: no row test
 #pragma unroll
-            for (int k = 0; k < 32 / S; ++k) {
-                const unsigned j = sidx + S * k;
-                if (j < cnt) {
-                    bool h0, h1;
-                    const float4 c = s_tri[warp][buf][j][3];
-                    near_line2(rp, make_float4(c.x, c.x, c.y, c.y), make_float4(c.z, c.z, c.w, c.w), h0, h1);
-                    m0 |= (unsigned)h0 << k;
-                    m1 |= (unsigned)h1 << k;
+                for (int k = 0; k < K; ++k) row(k);
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if ((unsigned)k >= kmax) break;
+                    row(k);
                 }
             }
+            const unsigned rows = kmax >= 32 ? 0xffffffffu : (1u << kmax) - 1u;
+            const unsigned m0 = ~x0 & rows, m1 = ~x1 & rows;
             // Moller-Trumbore on the survivors (o = -(-o) is exact)
             unsigned m = m0 | m1;
             while (m) {
                 const unsigned kk = __ffs(m) - 1;
                 m &= m - 1;
-                const unsigned j = sidx + S * kk;
+                const unsigned j = sidx + S * (kmax - 1 - kk);
                 const float4 A = s_tri[warp][buf][j][0], E1 = s_tri[warp][buf][j][1], E2 = s_tri[warp][buf][j][2];
                 float t;
                 if (((m0 >> kk) & 1u) &&

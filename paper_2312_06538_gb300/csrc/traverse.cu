@@ -453,42 +453,62 @@ __device__ __forceinline__ float4 chunk_sphere(float4 ts, bool valid) {
 // bounding sphere: eq. 9 is an exact sphere-against-region test, so a child
 // that rejects the bounding sphere rejects every triangle sphere inside it
 // (its word is 0) and only the children that accept it run the 32-lane tests.
+// 1024 threads per SM (64 registers): at 1536 threads (40 registers) the
+// pipeline's state spilled and the pass ran 2-3 % slower.
 template <class Parents, int BLK, bool WIDE>
-__global__ void __launch_bounds__(BLK, 1536 / BLK) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
+__global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
     pdl_wait();
     const WorkSplit ws(sb.totals[0], sb.work + 0, 16u, COUNT_BATCH);
     const int lane = threadIdx.x & 31;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned claim = ws.first_claim();
-    UnitStream<Parents> p0;
-    if (!p0.take(par, sb, ws, claim)) return;
+    // one cursor leads two units ahead of the tested one; the units in flight keep only
+    // their parent, first ballot word and the parent's triangle count
+    UnitStream<Parents> lead;
+    if (!lead.take(par, sb, ws, claim)) return;
+    struct Slot {
+        unsigned p, wo, len;
+    };
+    auto slot_of = [&]() { return Slot{lead.c.p, lead.c.ob + (lead.u - lead.c.ub), lead.c.len}; };
+    Slot s0 = slot_of();
     bool v0, v1 = false;
     float4 ts0 = zero;
     {
-        const unsigned t0 = p0.c.tri(par, p0.u, v0);
+        const unsigned t0 = lead.c.tri(par, lead.u, v0);
         if (v0) ts0 = tri_sphere[t0];
     }
-    UnitStream<Parents> p1 = p0;
-    bool has1 = p1.step(par, sb, ws, claim);
+    bool has1 = lead.step(par, sb, ws, claim);
+    Slot s1 = s0;
     unsigned t1 = 0;
-    if (has1) t1 = p1.c.tri(par, p1.u, v1);
+    if (has1) {
+        s1 = slot_of();
+        t1 = lead.c.tri(par, lead.u, v1);
+    }
+    // the tested unit's parent: its children (set when the parent changes)
+    unsigned cur_p = 0xffffffffu, nc = 0, a0 = 0;
     for (;;) {
         float4 ts1 = zero;
         if (v1) ts1 = tri_sphere[t1];
-        UnitStream<Parents> p2 = p1;
+        Slot s2 = s1;
         bool has2 = false, v2 = false;
         unsigned t2 = 0;
         if (has1) {
-            has2 = p2.step(par, sb, ws, claim);
-            if (has2) t2 = p2.c.tri(par, p2.u, v2);
+            has2 = lead.step(par, sb, ws, claim);
+            if (has2) {
+                s2 = slot_of();
+                t2 = lead.c.tri(par, lead.u, v2);
+            }
         }
-        const UnitCursor<Parents>& c0 = p0.c;
-        const unsigned nch = (c0.len + 31) >> 5, nc = par.nchild(c0.p);
-        const unsigned a0 = par.child_id(c0.p, 0);
+        if (s0.p != cur_p) {   // warp-uniform
+            cur_p = s0.p;
+            nc = par.nchild(cur_p);
+            a0 = par.child_id(cur_p, 0);
+        }
         const float4* csp = par.child.sphere + a0;
         const float4* cco = par.child.cone + a0;
         const float2* ctg = par.child.trig + a0;
-        unsigned* mw = sb.mask + c0.ob + (p0.u - c0.ub);
+        const unsigned nch = (s0.len + 31) >> 5;
+        unsigned* mw = sb.mask + s0.wo;
         if (Parents::kChunkCull) {
             const float4 K = chunk_sphere(ts0, v0);
             // children in groups of 32 (lane = child); more than one group only when B = 64
@@ -516,10 +536,10 @@ __global__ void __launch_bounds__(BLK, 1536 / BLK) k_count(Parents par, StageBuf
             }
         }
         if (!has1) break;
-        p0 = p1;
+        s0 = s1;
         v0 = v1;
         ts0 = ts1;
-        p1 = p2;
+        s1 = s2;
         has1 = has2;
         v1 = v2;
         t1 = t2;
