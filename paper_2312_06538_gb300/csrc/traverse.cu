@@ -457,9 +457,13 @@ __device__ __forceinline__ float4 chunk_sphere(float4 ts, bool valid) {
 // pipeline's state spilled and the pass ran 2-3 % slower.
 template <class Parents, int BLK, bool WIDE>
 __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
+    constexpr int NCH = WIDE ? 64 : 32;   // child slots per warp
+    // the tested parent's children, copied when the parent changes
+    __shared__ float4 s_sp[BLK / 32][NCH], s_co[BLK / 32][NCH];
+    __shared__ float2 s_tg[BLK / 32][NCH];
     pdl_wait();
     const WorkSplit ws(sb.totals[0], sb.work + 0, 16u, COUNT_BATCH);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned claim = ws.first_claim();
     // one cursor leads two units ahead of the tested one; the units in flight keep only
@@ -485,7 +489,10 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
         t1 = lead.c.tri(par, lead.u, v1);
     }
     // the tested unit's parent: its children (set when the parent changes)
-    unsigned cur_p = 0xffffffffu, nc = 0, a0 = 0;
+    unsigned cur_p = 0xffffffffu, nc = 0;
+    const float4* csp = s_sp[warp];
+    const float4* cco = s_co[warp];
+    const float2* ctg = s_tg[warp];
     for (;;) {
         float4 ts1 = zero;
         if (v1) ts1 = tri_sphere[t1];
@@ -502,11 +509,15 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
         if (s0.p != cur_p) {   // warp-uniform
             cur_p = s0.p;
             nc = par.nchild(cur_p);
-            a0 = par.child_id(cur_p, 0);
+            const unsigned a0 = par.child_id(cur_p, 0);
+            __syncwarp();      // the previous parent's children are no longer read
+            for (unsigned cl = lane; cl < nc; cl += 32) {
+                s_sp[warp][cl] = par.child.sphere[a0 + cl];
+                s_co[warp][cl] = par.child.cone[a0 + cl];
+                s_tg[warp][cl] = par.child.trig[a0 + cl];
+            }
+            __syncwarp();
         }
-        const float4* csp = par.child.sphere + a0;
-        const float4* cco = par.child.cone + a0;
-        const float2* ctg = par.child.trig + a0;
         const unsigned nch = (s0.len + 31) >> 5;
         unsigned* mw = sb.mask + s0.wo;
         if (Parents::kChunkCull) {
