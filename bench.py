@@ -298,12 +298,15 @@ def closest_traffic():
         return None
 
 
-def launches_per_step(levels: int, compress: bool) -> int:
+def launches_per_step(levels: int, compress: bool, words: bool = False) -> int:
     """Kernels of libcrsh.so launched by one pass (count of <<<>>> in the call sequence)."""
     # tables, gen, chunk (which also counts the digits) or hist, plan, 4 passes, pos, gather
     hash_sort = 1 + 1 + 1 + 1 + 4 + (1 if compress else 0) + 1
     build = max(1, levels - 1)   # level 1 (with level 2 merged in), then one per level above
-    traverse = 1 + 5 + 5 * (levels - 1) + 1   # mesh stage, top stage, 5 kernels per level, csr
+    if words and levels >= 2:    # mesh stage, top stage, 5 kernels per level above 1, unit scan + count at 1
+        traverse = 1 + 5 + 5 * (levels - 2) + 2
+    else:                        # mesh stage, top stage, 5 kernels per level, csr
+        traverse = 1 + 5 + 5 * (levels - 1) + 1
     closest = 3
     return hash_sort + build + traverse + closest
 
@@ -689,7 +692,7 @@ def run_gpu(args, w):
     dev = torch.device("cuda", torch.cuda.current_device())
     props = torch.cuda.get_device_properties(dev)
 
-    p = pl.workload_pipeline(w, device=dev)
+    p = pl.workload_pipeline(w, device=dev, level1_words=args.level1 == "words")
     hp, bp = pl.workload_params(w)
     g_host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
               pl.Pipeline.gbuffer_to_device(w.gbuffer, "cpu").items()}
@@ -806,7 +809,10 @@ def run_gpu(args, w):
     tr_ms = float(stage[:, 2].mean())
     eq9_tests = sum(c["tests"]) + c["mesh_tests"]
     traffic = closest_traffic()
-    roofline = {"kernel": "crsh_closest_hit (k_closest + fill + finalize)", "bound": "alu",
+    words = bool(p.level1_words)
+    roofline = {"kernel": ("crsh_closest_hit (k_closest_words: level-1 ballots gathered into groups, then tested; "
+                           "+ fill + finalize)") if words else "crsh_closest_hit (k_closest + fill + finalize)",
+                "bound": "alu",
                 "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
                 "traffic": traffic,
                 "peak_source": "measured: crsh_fma_probe (FP32 FMA chains at full occupancy, best of 5, burst)",
@@ -817,7 +823,9 @@ def run_gpu(args, w):
                                f"{c['final_tests']} candidate tests per launch"}
     # the traversal stage (its count, scan and emit kernels; k_count is its top kernel) against the
     # same FP32 peak: eq. 9 work of the tests the paper's count makes, per call
-    roofline_traverse = {"kernel": "crsh_traverse (k_count + k_emit + scans, all levels)", "bound": "alu",
+    roofline_traverse = {"kernel": ("crsh_traverse (k_count + k_emit + scans above level 1; level 1: count pass "
+                                    "and item descriptors)") if words else
+                                   "crsh_traverse (k_count + k_emit + scans, all levels)", "bound": "alu",
                          "achieved": eq9_tests * EQ9_FLOPS / (tr_ms * 1e-3) / 1e12, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": eq9_tests * EQ9_FLOPS / (tr_ms * 1e-3) / 1e12 / peak_tf,
                          "traffic": None,
@@ -830,6 +838,7 @@ def run_gpu(args, w):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene, software-rasterised G-buffer)",
         "config": {"workload": workload_description(w), "pixels": w.n_pixels, "triangles": w.scene.n_tris,
                    "rays_per_step": n_rays, "bundle": w.bundle, "levels": w.levels,
+                   "level1": "words" if p.level1_words else "list",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (512 MiB write outside the step events)"},
         "level_counts": {"levels": "index l-1 = level l (Tables 1-3 schema)", "tests": list(map(int, c["tests"])),
@@ -849,7 +858,7 @@ def run_gpu(args, w):
         "roofline": roofline,
         "roofline_traverse": roofline_traverse,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step(w.levels, True) * args.steps,
+        "gpu_launches": launches_per_step(w.levels, True, bool(p.level1_words)) * args.steps,
         "clocks": clocks,
     }
     if not args.no_comparators:
@@ -892,6 +901,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--res", type=int, default=None)
+    ap.add_argument("--level1", default="words", choices=["words", "list"],
+                    help="level 1 of the traversal in word form (read by the final tests from the ballots) "
+                         "or as a written (node, triangle) list")
     ap.add_argument("--ref-crop", type=int, default=64)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -170,14 +170,37 @@ typedef struct {
     uint32_t block_threads;          /* block shape of the traversal's test and emit passes: 128,
                                         256 or 512 threads (0 = 256); a tuning knob, results do
                                         not depend on it */
+    uint32_t level1_words;           /* 1: leave level 1 in word form (crsh_pairs.words) instead
+                                        of writing its (node, triangle) pairs; hierarchies of two
+                                        or more levels only */
 } crsh_traverse_params;
 
-/* Level-1 (node, triangle) pairs grouped by node, triangles ascending. */
+/* Level-1 candidates in word form, written by crsh_traverse with
+ * level1_words = 1 and read by crsh_closest_hit: the same set of (node,
+ * triangle) pairs as the list form, kept as the 32-bit ballots of the
+ * traversal's last test pass.  Work item i is items[4 i .. 4 i + 3] =
+ * (level-1 node n, position r in `tri`, first word w, word count c <= 32):
+ * for j < c, bit b of words[w + j] set means node n accepted triangle
+ * tri[r + 32 j + b].  Every pair belongs to exactly one item.  The arrays
+ * live in the traversal's workspace: the form is valid until that workspace
+ * is written again. */
 typedef struct {
-    uint32_t *node, *tri;            /* capacity entries each */
-    uint32_t *node_offsets;          /* level-1 node count + 1 entries: CSR over nodes */
-    uint32_t *count;                 /* device: pairs written */
+    const uint32_t *words;
+    const uint32_t *tri;             /* level-2 pair list, triangle column */
+    const uint32_t *items;           /* 4 entries per work item */
+    const uint32_t *n_items;         /* device: work items */
+    uint32_t valid;                  /* 1 when the fields above describe level 1 */
+    uint32_t reserved;
+} crsh_pair_words;
+
+/* Level-1 (node, triangle) pairs grouped by node, triangles ascending, or
+ * (level1_words) their word form. */
+typedef struct {
+    uint32_t *node, *tri;            /* capacity entries each (not written in word form) */
+    uint32_t *node_offsets;          /* level-1 node count + 1 entries: CSR over nodes (list form) */
+    uint32_t *count;                 /* device: pairs written (list form) */
     uint64_t capacity;               /* 1 .. 2^31 */
+    crsh_pair_words words;           /* output of crsh_traverse: valid = 1 in word form, else 0 */
 } crsh_pairs;
 
 /* Closest hits in generation order (ray_id). tri = -1: no hit (t = u = v = 0). */
@@ -331,7 +354,11 @@ size_t crsh_traverse_workspace(const crsh_hierarchy *h, uint32_t n_tris, uint32_
  * expands to the children of p, each tested against t.  Every level's list is
  * compacted in order.  Output: level-1 pairs grouped by node (out), counters
  * tests, hits, tests_paper, mesh_tests, mesh_hits and needed_pairs (reset by this call).  A list
- * longer than out->capacity sets CRSH_ERR_CAPACITY and needed_pairs. */
+ * longer than out->capacity sets CRSH_ERR_CAPACITY and needed_pairs.  With
+ * params->level1_words (two or more levels) level 1 is left in word form:
+ * out->words is filled (valid = 1), out->node, tri, node_offsets and count are
+ * not written, and the workspace must stay untouched until crsh_closest_hit
+ * has read it; otherwise out->words.valid is set to 0. */
 crsh_status crsh_traverse(const crsh_hierarchy *h, const crsh_scene *scene,
                           const crsh_traverse_params *params, crsh_pairs *out,
                           crsh_counters *counters, void *workspace, size_t workspace_bytes,
@@ -340,7 +367,8 @@ crsh_status crsh_traverse(const crsh_hierarchy *h, const crsh_scene *scene,
 /* Workspace bytes crsh_closest_hit / crsh_bruteforce_closest_hit need. */
 size_t crsh_closest_hit_workspace(uint32_t ray_capacity);
 
-/* Section 3.3.8.  For every level-1 pair (n, t) and every ray of n:
+/* Section 3.3.8.  For every level-1 pair (n, t) (the list of pairs->node and
+ * pairs->tri, or pairs->words when its valid flag is set) and every ray of n:
  * Moller-Trumbore in FP32 (two-sided, inclusive edges, 0 < t <= t_max); the
  * closest hit per ray is the smallest (t, triangle id).  The (t, u, v) of the
  * winning triangle are then recomputed in double-word (float + float, about

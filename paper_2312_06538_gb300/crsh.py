@@ -62,11 +62,16 @@ class crsh_hierarchy(ctypes.Structure):
 
 
 class crsh_traverse_params(ctypes.Structure):
-    _fields_ = [("mesh_cull", U32), ("block_threads", U32)]
+    _fields_ = [("mesh_cull", U32), ("block_threads", U32), ("level1_words", U32)]
+
+
+class crsh_pair_words(ctypes.Structure):
+    _fields_ = [("words", P), ("tri", P), ("items", P), ("n_items", P), ("valid", U32), ("reserved", U32)]
 
 
 class crsh_pairs(ctypes.Structure):
-    _fields_ = [("node", P), ("tri", P), ("node_offsets", P), ("count", P), ("capacity", U64)]
+    _fields_ = [("node", P), ("tri", P), ("node_offsets", P), ("count", P), ("capacity", U64),
+                ("words", crsh_pair_words)]
 
 
 class crsh_hits(ctypes.Structure):

@@ -43,6 +43,13 @@ bool hier_ok(const crsh_hierarchy* h) {
     return true;
 }
 
+// the word form is either absent (valid = 0) or complete
+static bool words_ok(const crsh_pair_words& w, const crsh_hierarchy* h) {
+    if (!w.valid) return true;
+    if (w.valid != 1 || h->levels < 2) return false;
+    return w.words && w.tri && w.items && w.n_items;
+}
+
 bool scene_ok(const crsh_scene* s, bool need_prepared) {
     if (!s || !s->v0x || !s->v0y || !s->v0z || !s->v1x || !s->v1y || !s->v1z || !s->v2x || !s->v2y || !s->v2z)
         return false;
@@ -221,6 +228,7 @@ crsh_status crsh_traverse(const crsh_hierarchy* h, const crsh_scene* scene, cons
     if (!hier_ok(h) || !scene_ok(scene, true) || !p || !out || !counters || !ws_ok(workspace)) return CRSH_ERR_INVALID_ARG;
     if (p->block_threads != 0 && p->block_threads != 128 && p->block_threads != 256 && p->block_threads != 512)
         return CRSH_ERR_INVALID_ARG;
+    if (p->level1_words > 1) return CRSH_ERR_INVALID_ARG;
     if (!out->node || !out->tri || !out->node_offsets || !out->count || out->capacity == 0 ||
         out->capacity > (1ull << 31))
         return CRSH_ERR_INVALID_ARG;
@@ -238,6 +246,7 @@ crsh_status crsh_closest_hit(const crsh_hierarchy* h, const crsh_rays* rays, con
     if (!hier_ok(h) || !rays_ok(rays) || !n_rays || !scene_ok(scene, true) || !pairs || !pairs->node ||
         !pairs->tri || !pairs->count || !out || !out->tri || !out->t || !out->u || !out->v || !counters || !ws_ok(workspace))
         return CRSH_ERR_INVALID_ARG;
+    if (!words_ok(pairs->words, h)) return CRSH_ERR_INVALID_ARG;
     DeviceInfo dev;
     if (!current_device(dev)) return CRSH_ERR_CUDA;
     return closest_hit_launch(h, rays, n_rays, scene, pairs, out, counters, workspace, workspace_bytes,
@@ -250,6 +259,7 @@ crsh_status crsh_closest_hit_noalloc(const crsh_hierarchy* h, const crsh_rays* r
     if (!hier_ok(h) || !rays_ok(rays) || !n_rays || !scene_ok(scene, true) || !pairs || !pairs->node ||
         !pairs->tri || !pairs->count || !out || !out->tri || !out->t || !out->u || !out->v || !counters)
         return CRSH_ERR_INVALID_ARG;
+    if (!words_ok(pairs->words, h)) return CRSH_ERR_INVALID_ARG;
     if (rays->capacity > CRSH_NOALLOC_MAX_RAYS) return CRSH_ERR_INVALID_ARG;
     DeviceInfo dev;
     if (!current_device(dev)) return CRSH_ERR_CUDA;

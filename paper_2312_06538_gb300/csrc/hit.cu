@@ -346,6 +346,252 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest(const uint32_t* pnode, 
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->final_tests_paper = (unsigned long long)P * B;
 }
 
+// ---------------------------------------------------------------------------
+// Final tests over the word form of level 1 (crsh_pair_words): the same
+// candidate set, read from the traversal's last ballots instead of a written
+// pair list.  Warps claim batches of work items (one child's run of up to 32
+// chunk ballots; a node's items are consecutive), load the batch's
+// descriptors at once, and for each item scan its words, copy the triangle
+// ids of the set bits from the parent list into a ring in shared memory
+// (cp.async), and cut the ring into groups of up to 32 triangles of one node.
+// Each group runs k_closest's group test; the next group is gathered and its
+// records copied while the current one is tested, and each item's words are
+// loaded while the item before it is gathered.
+// ---------------------------------------------------------------------------
+constexpr unsigned WI_BATCH = 8;   // work items per claim (at most 32)
+
+template <int B>
+__global__ void __launch_bounds__(CH_BLOCK, 8) k_closest_words(crsh_pair_words pw, RaysDev rays,
+                                                               const unsigned* n_ptr, unsigned n_cap,
+                                                               const float4* tri_mt, unsigned long long* best,
+                                                               unsigned* work, crsh_counters* ctr) {
+    pdl_wait();
+    constexpr int H = B / 2;            // lanes per node (two rays each)
+    constexpr int S = 32 / H;           // streams
+    constexpr int K = 32 / S;           // pre-test rows of a full group
+    __shared__ __align__(16) float4 s_tri[CH_WARPS][2][32][4];    // (a, n.x) (e1, n.y) (e2, n.z) (c, q)
+    __shared__ unsigned s_tid[CH_WARPS][2][32];
+    __shared__ unsigned s_q[CH_WARPS][64];                         // ring of gathered triangle ids
+    const unsigned N = min(*n_ptr, n_cap);   // rays past the capacity are never touched
+    const unsigned I = *pw.n_items;
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    const uint4* items = reinterpret_cast<const uint4*>(pw.items);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    const int r = lane % H, sidx = lane / H;
+    unsigned long long n_tests = 0, n_hits = 0;
+    // ---- producer: items -> words -> triangle ids -> groups (warp-uniform but the per-lane values) ----
+    // batches of items from the counter: lane 0 holds the next one (start, size), claimed one
+    // batch ahead; sizes shrink toward the end (about a quarter of the items left per warp)
+    unsigned cl_base = 0, cl_size = WI_BATCH;
+    if (lane == 0) cl_base = atomicAdd(work, WI_BATCH);
+    uint4 desc = make_uint4(0, 0, 0, 0);       // lane j < nb: item j of the batch
+    unsigned nb = 0, ib = 0;                   // items in the batch, next item of it
+    unsigned node = 0, rs = 0;                 // current item: level-1 node, run position of its first chunk
+    unsigned wl = 0, any = 0;                  // its words (this lane's), nonzero words left
+    unsigned wnext = 0;                        // the next item's words (this lane's), loaded ahead
+    unsigned qh = 0, qn = 0, qnode = 0;        // ring head, ids queued, their node
+    bool more = true;
+    auto words_of = [&](unsigned j) -> unsigned {   // lane's word of batch item j (j < nb)
+        const unsigned w0 = __shfl_sync(FULL, desc.z, j), c = __shfl_sync(FULL, desc.w, j);
+        return (unsigned)lane < c ? pw.words[w0 + lane] : 0u;
+    };
+    auto claim_batch = [&]() -> bool {
+        const unsigned base = __shfl_sync(FULL, cl_base, 0), size = __shfl_sync(FULL, cl_size, 0);
+        if (base >= I) return false;
+        if (lane == 0) {
+            const unsigned done = base + size, left = done < I ? I - done : 0u;
+            cl_size = max(1u, min(WI_BATCH, left / (4u * nw)));
+            cl_base = atomicAdd(work, cl_size);
+        }
+        nb = min(size, I - base);
+        if ((unsigned)lane < nb) desc = items[base + lane];
+        ib = 0;
+        wnext = words_of(0);
+        return true;
+    };
+    // the next item (its words were loaded ahead); false when the warp's work is done
+    auto next_item = [&]() -> bool {
+        if (ib >= nb && !claim_batch()) return false;
+        node = __shfl_sync(FULL, desc.x, ib);
+        rs = __shfl_sync(FULL, desc.y, ib);
+        wl = wnext;
+        any = __ballot_sync(FULL, wl != 0);
+        ++ib;
+        if (ib < nb) wnext = words_of(ib);
+        return true;
+    };
+    // Groups are made one step ahead of their use: gather() issues the copies of
+    // the next group's triangle ids into the ring and records the group (its
+    // size and node); emit() later waits for those copies (issued a group test
+    // earlier) and starts the copies of the group's triangle records.
+    unsigned pend_cnt = 0, pend_node = 0;      // the gathered group not yet emitted
+    auto gather = [&]() {
+        pend_cnt = 0;
+        for (;;) {
+            if (qn >= 32) {   // a full group (ids past it stay for the next one)
+                pend_cnt = 32;
+                pend_node = qnode;
+                return;
+            }
+            if (any) {   // the triangle ids of the item's nonzero words, copied into the ring
+                do {
+                    const unsigned kk = __ffs(any) - 1;
+                    any &= any - 1;
+                    const unsigned m = __shfl_sync(FULL, wl, kk);
+                    if ((m >> lane) & 1u)
+                        cp_async4(&s_q[warp][(qh + qn + __popc(m & lt)) & 63], pw.tri + rs + 32 * kk + lane);
+                    qn += __popc(m);
+                } while (any && qn < 32);
+                continue;
+            }
+            if (more && (qn == 0 || node == qnode)) {
+                more = next_item();
+                if (more && qn == 0) qnode = node;
+                if (more && node == qnode) continue;
+            }
+            // a new node (or the end) closes the ring's group
+            pend_cnt = qn;
+            pend_node = qnode;
+            return;
+        }
+    };
+    // stage the gathered group's ids as triangle records into buffer b (one commit)
+    auto emit = [&](int b) {
+        const unsigned cnt = pend_cnt;
+        cp_async_wait_all();
+        __syncwarp();
+        if ((unsigned)lane < cnt) {
+            const unsigned t = s_q[warp][(qh + lane) & 63];
+            const float4* m = tri_mt + 4 * (size_t)t;
+            cp_async16(&s_tri[warp][b][lane][0], m);
+            cp_async16(&s_tri[warp][b][lane][1], m + 1);
+            cp_async16(&s_tri[warp][b][lane][2], m + 2);
+            cp_async16(&s_tri[warp][b][lane][3], m + 3);
+            s_tid[warp][b][lane] = t;
+        } else {
+            // past the group: a sphere no line passes through (q = -inf)
+            s_tri[warp][b][lane][3] = make_float4(0.f, 0.f, 0.f, __int_as_float(0xff800000));
+        }
+        cp_async_commit();
+        __syncwarp();   // the ring slots just read may be refilled
+        qh = (qh + cnt) & 63;
+        qn -= cnt;
+        if (qn == 0) qnode = node;   // a closed node: the ring continues with the current item's
+    };
+    gather();
+    unsigned cnt = pend_cnt, gnode = pend_node;
+    if (cnt) {
+        emit(0);
+        gather();
+        // the node's two rays of this lane (a missing ray gets kid2 = NaN:
+        // its pre-tests all fail)
+        RayPair rp;
+        float ta = 0.f, tb = 0.f;
+        unsigned cur, ray0, ray1;
+        bool v0, v1;
+        auto enter_node = [&](unsigned nd) {
+            cur = nd;
+            ray0 = cur * B + r;
+            ray1 = ray0 + H;
+            v0 = ray0 < N;
+            v1 = ray1 < N;
+            float ax = 0, ay = 0, az = 0, adx = 0, ady = 0, adz = 0;
+            float bx = 0, by = 0, bz = 0, bdx = 0, bdy = 0, bdz = 0;
+            ta = tb = 0.f;
+            if (v0) {
+                ax = rays.ox[ray0]; ay = rays.oy[ray0]; az = rays.oz[ray0];
+                adx = rays.dx[ray0]; ady = rays.dy[ray0]; adz = rays.dz[ray0]; ta = rays.tmax[ray0];
+            }
+            if (v1) {
+                bx = rays.ox[ray1]; by = rays.oy[ray1]; bz = rays.oz[ray1];
+                bdx = rays.dx[ray1]; bdy = rays.dy[ray1]; bdz = rays.dz[ray1]; tb = rays.tmax[ray1];
+            }
+            rp.nox = make_float2(-ax, -bx); rp.noy = make_float2(-ay, -by); rp.noz = make_float2(-az, -bz);
+            rp.dx = make_float2(adx, bdx); rp.dy = make_float2(ady, bdy); rp.dz = make_float2(adz, bdz);
+            rp.kid2 = make_float2(v0 ? ray_kid2(adx, ady, adz) : __int_as_float(0x7fc00000),
+                                  v1 ? ray_kid2(bdx, bdy, bdz) : __int_as_float(0x7fc00000));
+        };
+        enter_node(gnode);
+        unsigned long long k0 = NO_HIT, k1 = NO_HIT;
+        int buf = 0;
+        for (;;) {
+            // the next group's records into the other buffer, then the ids of the one after it
+            const unsigned ncnt = pend_cnt, nnode = pend_node;
+            if (ncnt) {
+                emit(buf ^ 1);
+                gather();
+            } else {
+                cp_async_commit();   // keeps "all but the newest group" meaning this group
+            }
+            cp_async_wait_prev();
+            __syncwarp();
+            const unsigned nrays = min((unsigned)B, N - cur * B);
+            if (lane == 0) n_tests += (unsigned long long)cnt * nrays;
+            // the group test of k_closest
+            const unsigned kmax = (cnt + S - 1) / S;
+            unsigned x0 = 0, x1 = 0;
+            auto row = [&](int k) {
+                const float4 c = s_tri[warp][buf][sidx + S * k][3];
+                const float2 d = near_line2_margin(rp, make_float4(c.x, c.x, c.y, c.y), make_float4(c.z, c.z, c.w, c.w));
+                x0 = __funnelshift_l(__float_as_uint(d.x), x0, 1);
+                x1 = __funnelshift_l(__float_as_uint(d.y), x1, 1);
+            };
+            if (kmax == (unsigned)K) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) row(k);
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if ((unsigned)k >= kmax) break;
+                    row(k);
+                }
+            }
+            const unsigned rows = kmax >= 32 ? 0xffffffffu : (1u << kmax) - 1u;
+            const unsigned m0 = ~x0 & rows, m1 = ~x1 & rows;
+            unsigned m = m0 | m1;
+            while (m) {
+                const unsigned kk = __ffs(m) - 1;
+                m &= m - 1;
+                const unsigned j = sidx + S * (kmax - 1 - kk);
+                const float4 A = s_tri[warp][buf][j][0], E1 = s_tri[warp][buf][j][1], E2 = s_tri[warp][buf][j][2];
+                float t;
+                if (((m0 >> kk) & 1u) &&
+                    mt_hit(-rp.nox.x, -rp.noy.x, -rp.noz.x, rp.dx.x, rp.dy.x, rp.dz.x, ta, A, E1, E2, t)) {
+                    ++n_hits;
+                    const unsigned long long key = hit_key(t, s_tid[warp][buf][j]);
+                    k0 = key < k0 ? key : k0;
+                }
+                if (((m1 >> kk) & 1u) &&
+                    mt_hit(-rp.nox.y, -rp.noy.y, -rp.noz.y, rp.dx.y, rp.dy.y, rp.dz.y, tb, A, E1, E2, t)) {
+                    ++n_hits;
+                    const unsigned long long key = hit_key(t, s_tid[warp][buf][j]);
+                    k1 = key < k1 ? key : k1;
+                }
+            }
+            __syncwarp();   // buffer buf is refilled two groups on
+            if (!ncnt) break;
+            if (nnode != cur) {
+                flush_best<H>(k0, v0, sidx, ray0, best);
+                flush_best<H>(k1, v1, sidx, ray1, best);
+                enter_node(nnode);
+                k0 = k1 = NO_HIT;
+            }
+            cnt = ncnt;
+            buf ^= 1;
+        }
+        flush_best<H>(k0, v0, sidx, ray0, best);
+        flush_best<H>(k1, v1, sidx, ray1, best);
+    }
+    n_tests = warp_sum64(n_tests);
+    n_hits = warp_sum64(n_hits);
+    if (lane == 0) {
+        if (n_tests) atomicAdd(&ctr->final_tests, n_tests);
+        if (n_hits) atomicAdd(&ctr->final_hits, n_hits);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->final_tests_paper = ctr->hits[0] * B;
+}
+
 // n_cap: rays the scratch and the ray arrays hold; a larger device count is
 // clamped to it and reported as CRSH_ERR_CAPACITY (no access past the end)
 __global__ void k_fill_best(unsigned long long* best, const unsigned* n_ptr, unsigned n_cap, unsigned* work,
@@ -517,6 +763,19 @@ static void launch_closest(const crsh_pairs* pairs, const RaysDev& rd, const uin
     if (b <= 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_closest<B>, CH_BLOCK, 0) != cudaSuccess || b <= 0) b = 1;
         per_sm[d].store(b, std::memory_order_relaxed);
+    }
+    if (pairs->words.valid) {
+        static std::atomic<int> per_sm_w[64];
+        int bw = per_sm_w[d].load(std::memory_order_relaxed);
+        if (bw <= 0) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_closest_words<B>, CH_BLOCK, 0) != cudaSuccess ||
+                bw <= 0)
+                bw = 1;
+            per_sm_w[d].store(bw, std::memory_order_relaxed);
+        }
+        launch_pdl(k_closest_words<B>, dev.sms * bw, CH_BLOCK, 0, s, pairs->words, rd, n_rays, n_cap, mt, best, work,
+                   ctr);
+        return;
     }
     launch_pdl(k_closest<B>, dev.sms * b, CH_BLOCK, 0, s, pairs->node, pairs->tri, pairs->count, pairs->capacity, rd,
                n_rays, n_cap, mt, best, work, ctr);

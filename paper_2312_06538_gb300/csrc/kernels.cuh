@@ -10,6 +10,11 @@
 
 namespace crsh {
 
+// Words per final-test work item of the word form of level 1 (crsh_pair_words):
+// an item is one child's run of up to WORD_SEG consecutive chunk ballots, so a
+// node with a long row is split over several items.
+constexpr unsigned WORD_SEG = 32;
+
 struct DeviceInfo {
     int device = -1;
     int sms = 0;

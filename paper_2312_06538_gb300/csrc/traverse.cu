@@ -238,7 +238,8 @@ struct TopParents {             // parents: accepted (top node, mesh) pairs, gro
 struct StageBuf {
     unsigned* ubase;            // per parent: first unit        (n + 1 entries)
     unsigned* obase;            // per parent: first ballot word (n + 1 entries)
-    unsigned* totals;           // [0] units, [1] ballot words
+    unsigned* ibase;            // per parent: first final-test work item of the word form (n + 1 entries)
+    unsigned* totals;           // [0] units, [1] ballot words, [2] work items
     unsigned* mask;             // ballot words in output order (parent, child, chunk)
     unsigned* pos;              // exclusive prefix of the ballot popcounts (O + 1 entries)
     unsigned* bsum;             // per scan block: accepted pairs
@@ -253,17 +254,19 @@ struct RunOut {
 };
 
 // Single block: exclusive scans over the parents of units (chunks of 32
-// triangles) and ballot words (children x chunks); the stage's test counters.
+// triangles), ballot words (children x chunks) and the work items of the
+// word form's final tests (children x segments of WORD_SEG chunks); the
+// stage's test counters.
 template <class Parents>
 __global__ void __launch_bounds__(1024) k_unit_scan(Parents par, StageBuf sb, crsh_counters* ctr, int level_idx,
                                                     unsigned B_paper) {
     pdl_wait();
-    __shared__ unsigned long long s_w[32][4];
-    __shared__ unsigned long long s_tot[4];
+    __shared__ unsigned long long s_w[32][5];
+    __shared__ unsigned long long s_tot[5];
     const unsigned n = par.count();
     const unsigned per = (n + blockDim.x - 1) / blockDim.x;
     const unsigned b0 = min(n, threadIdx.x * per), b1 = min(n, b0 + per);
-    unsigned long long u = 0, o = 0, tests = 0, paper = 0;
+    unsigned long long u = 0, o = 0, it = 0, tests = 0, paper = 0;
     for (unsigned p = b0; p < b1; ++p) {
         unsigned s, len;
         par.range(p, s, len);
@@ -271,48 +274,57 @@ __global__ void __launch_bounds__(1024) k_unit_scan(Parents par, StageBuf sb, cr
         const unsigned nc = par.nchild(p);
         u += nch;
         o += (unsigned long long)nc * nch;
+        it += (unsigned long long)nc * ((nch + WORD_SEG - 1) / WORD_SEG);
         tests += (unsigned long long)nc * len;
         paper += len;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long iu = u, io = o;
+    unsigned long long iu = u, io = o, ii = it;
     for (int d = 1; d < 32; d <<= 1) {
-        unsigned long long a = __shfl_up_sync(FULL, iu, d), b = __shfl_up_sync(FULL, io, d);
-        if (lane >= d) { iu += a; io += b; }
+        unsigned long long a = __shfl_up_sync(FULL, iu, d), b = __shfl_up_sync(FULL, io, d),
+                           c = __shfl_up_sync(FULL, ii, d);
+        if (lane >= d) { iu += a; io += b; ii += c; }
     }
     const unsigned long long st = warp_sum64(tests), sp = warp_sum64(paper);
-    if (lane == 31) { s_w[warp][0] = iu; s_w[warp][1] = io; }
+    if (lane == 31) { s_w[warp][0] = iu; s_w[warp][1] = io; s_w[warp][4] = ii; }
     if (lane == 0) { s_w[warp][2] = st; s_w[warp][3] = sp; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long a = 0, b = 0, t = 0, q = 0;
+        unsigned long long a = 0, b = 0, c = 0, t = 0, q = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            const unsigned long long x = s_w[w][0], y = s_w[w][1];
+            const unsigned long long x = s_w[w][0], y = s_w[w][1], z = s_w[w][4];
             t += s_w[w][2];
             q += s_w[w][3];
             s_w[w][0] = a;
             s_w[w][1] = b;
+            s_w[w][4] = c;
             a += x;
             b += y;
+            c += z;
         }
-        s_tot[0] = a; s_tot[1] = b; s_tot[2] = t; s_tot[3] = q;
+        s_tot[0] = a; s_tot[1] = b; s_tot[2] = t; s_tot[3] = q; s_tot[4] = c;
     }
     __syncthreads();
-    unsigned long long ru = s_w[warp][0] + iu - u, ro = s_w[warp][1] + io - o;
+    unsigned long long ru = s_w[warp][0] + iu - u, ro = s_w[warp][1] + io - o, ri = s_w[warp][4] + ii - it;
     for (unsigned p = b0; p < b1; ++p) {
         unsigned s, len;
         par.range(p, s, len);
         const unsigned nch = (len + 31) >> 5;
+        const unsigned nc = par.nchild(p);
         sb.ubase[p] = (unsigned)ru;
         sb.obase[p] = (unsigned)ro;
+        sb.ibase[p] = (unsigned)ri;
         ru += nch;
-        ro += (unsigned long long)par.nchild(p) * nch;
+        ro += (unsigned long long)nc * nch;
+        ri += (unsigned long long)nc * ((nch + WORD_SEG - 1) / WORD_SEG);
     }
     if (threadIdx.x == 0) {
         sb.ubase[n] = (unsigned)s_tot[0];
         sb.obase[n] = (unsigned)s_tot[1];
+        sb.ibase[n] = (unsigned)s_tot[4];
         sb.totals[0] = (unsigned)s_tot[0];
         sb.totals[1] = (unsigned)s_tot[1];
+        sb.totals[2] = (unsigned)s_tot[4];
         ctr->tests[level_idx] = s_tot[2];
         ctr->tests_paper[level_idx] = B_paper ? (unsigned long long)B_paper * s_tot[3] : s_tot[3];
     }
@@ -456,7 +468,8 @@ __device__ __forceinline__ float4 chunk_sphere(float4 ts, bool valid) {
 // 1024 threads per SM (64 registers): at 1536 threads (40 registers) the
 // pipeline's state spilled and the pass ran 2-3 % slower.
 template <class Parents, int BLK, bool WIDE>
-__global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf sb, const float4* tri_sphere) {
+__global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf sb, const float4* tri_sphere,
+                                                          unsigned long long* popsum) {
     constexpr int NCH = WIDE ? 64 : 32;   // child slots per warp
     // the tested parent's children, copied when the parent changes
     __shared__ float4 s_sp[BLK / 32][NCH], s_co[BLK / 32][NCH];
@@ -490,6 +503,7 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
     }
     // the tested unit's parent: its children (set when the parent changes)
     unsigned cur_p = 0xffffffffu, nc = 0;
+    unsigned long long accepted = 0;   // pairs accepted by this warp (word form's level count)
     const float4* csp = s_sp[warp];
     const float4* cco = s_co[warp];
     const float2* ctg = s_tg[warp];
@@ -536,6 +550,7 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
                     const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
                     const unsigned m = __ballot_sync(FULL, ok);
                     if (lane == 0) mw[c * nch] = m;
+                    accepted += __popc(m);
                 }
             }
         } else {
@@ -544,6 +559,7 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
                 const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
                 const unsigned m = __ballot_sync(FULL, ok);
                 if (lane == 0) mw[c * nch] = m;
+                accepted += __popc(m);
             }
         }
         if (!has1) break;
@@ -555,6 +571,7 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
         v1 = v2;
         t1 = t2;
     }
+    if (popsum && lane == 0 && accepted) atomicAdd(popsum, accepted);
 }
 
 constexpr int SC_BLOCK = 256, SC_ITEMS = 8, SC_TILE = SC_BLOCK * SC_ITEMS, SC_GRID_MAX = 2048;
@@ -740,6 +757,30 @@ __global__ void __launch_bounds__(BLK) k_emit(Parents par, StageBuf sb, PairOut 
     }
 }
 
+// Word form of level 1: one descriptor per final-test work item (level-2
+// node p, child c, segment s of WORD_SEG chunks), written at item_base[p] +
+// c * segments + s: (level-1 node, position in the parent list of the
+// segment's first chunk, index of its first ballot word, word count).  One
+// warp per parent.
+__global__ void k_items(LevelParents par, StageBuf sb, uint4* items) {
+    pdl_wait();
+    const unsigned n = par.count(), cc = *par.n_child;
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += (gridDim.x * blockDim.x) >> 5) {
+        unsigned s, len;
+        par.range(p, s, len);
+        const unsigned nch = (len + 31) >> 5, nseg = (nch + WORD_SEG - 1) / WORD_SEG;
+        const unsigned first = p << par.logB;
+        const unsigned nc = first >= cc ? 0u : min(1u << par.logB, cc - first);
+        const unsigned ob = sb.obase[p], ib = sb.ibase[p];
+        for (unsigned c = 0; c < nc; ++c)
+            for (unsigned g = lane; g < nseg; g += 32) {
+                const unsigned k = g * WORD_SEG;
+                items[ib + c * nseg + g] = make_uint4(first + c, s + 32 * k, ob + c * nch + k, min(WORD_SEG, nch - k));
+            }
+    }
+}
+
 // CSR offsets (n + 1) of the node-sorted level-1 list: a node's offset is the
 // start of its run; a node without pairs takes the start of the next node
 // with pairs (the list end if none).  A few steps forward over the runs find
@@ -790,6 +831,7 @@ struct Carve {
 
 struct TvWs {
     uint32_t* bufT[2];                   // ping-pong pair lists (triangles) of the levels above 1
+    uint4* items;                        // word form of level 1: work item descriptors
     uint32_t *mpN, *mpM;                 // accepted (node, mesh)
     RunOut runs[CRSH_MAX_LEVELS];        // pair runs per level
     StageBuf sb;
@@ -820,6 +862,9 @@ TvWs carve_tv(void* ws, const crsh_hierarchy* h, uint32_t n_tris, uint32_t n_mes
     }
     w.sb.ubase = c.take<unsigned>(max_parents + 1);
     w.sb.obase = c.take<unsigned>(max_parents + 1);
+    w.sb.ibase = c.take<unsigned>(max_parents + 1);
+    // word form: an item covers at most WORD_SEG words and every (parent, child) row starts one
+    w.items = c.take<uint4>(max_words / WORD_SEG + (size_t)B * max_parents + 1);
     w.sb.totals = c.take<unsigned>(4);
     w.sb.mask = c.take<unsigned>(max_words + 1);
     w.sb.pos = c.take<unsigned>(max_words + 1);
@@ -870,7 +915,7 @@ static unsigned resident_blocks(K kernel, int block, const DeviceInfo& dev) {
 template <int BLK, bool WIDE, class Parents>
 static void run_stage(const Parents& par, const TvWs& w, unsigned stage, const float4* tsph, PairOut out,
                       RunOut runs, crsh_counters* ctr, int level_idx, unsigned B_paper, const DeviceInfo& dev,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool words_only = false) {
     StageBuf sb = w.sb;
     sb.work = w.work + 2 * stage;
     const unsigned sg = std::min<unsigned>(SC_GRID_MAX, dev.sms * 8);
@@ -878,7 +923,14 @@ static void run_stage(const Parents& par, const TvWs& w, unsigned stage, const f
     const unsigned gc = dev.sms * resident_blocks(k_count<Parents, BLK, WIDE>, BLK, dev);
     const unsigned ge = dev.sms * resident_blocks(k_emit<Parents, BLK, WIDE>, BLK, dev);
     launch_pdl(k_unit_scan<Parents>, 1, 1024, 0, s, par, sb, ctr, level_idx, B_paper);
-    launch_pdl(k_count<Parents, BLK, WIDE>, gc, BLK, 0, s, par, sb, tsph);
+    // word form (level 1 only): the ballots are the output, their popcounts the level's count
+    launch_pdl(k_count<Parents, BLK, WIDE>, gc, BLK, 0, s, par, sb, tsph,
+               words_only ? &ctr->hits[level_idx] : (unsigned long long*)nullptr);
+    if (words_only) {
+        if constexpr (std::is_same<Parents, LevelParents>::value)
+            launch_pdl(k_items, dev.sms * 8, 256, 0, s, par, sb, w.items);
+        return;
+    }
     launch_pdl(k_reduce, sg, SC_BLOCK, 0, s, sb);
     launch_pdl(k_wordscan, sg, SC_BLOCK, 0, s, sb, out, ctr, level_idx);
     launch_pdl(k_emit<Parents, BLK, WIDE>, ge, BLK, 0, s, par, sb, out, runs);
@@ -918,26 +970,34 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     TopParents top{w.mpN, w.mpM, &w.counts[0], sc->mesh_first_tri, level_nodes(L)};
     // the block shape, and for the level stages whether a parent has more
     // than 32 children (B = 64); the top stage has one child per parent
-    auto stage = [&](const auto& par, unsigned st, PairOut o, RunOut rn, int li, unsigned Bp, auto wide) {
+    auto stage = [&](const auto& par, unsigned st, PairOut o, RunOut rn, int li, unsigned Bp, auto wide,
+                     bool words_only) {
         constexpr bool W = decltype(wide)::value;
         switch (tp->block_threads) {
-            case 128: run_stage<128, W>(par, w, st, tsph, o, rn, ctr, li, Bp, dev, s); break;
-            case 512: run_stage<512, W>(par, w, st, tsph, o, rn, ctr, li, Bp, dev, s); break;
-            default: run_stage<256, W>(par, w, st, tsph, o, rn, ctr, li, Bp, dev, s); break;
+            case 128: run_stage<128, W>(par, w, st, tsph, o, rn, ctr, li, Bp, dev, s, words_only); break;
+            case 512: run_stage<512, W>(par, w, st, tsph, o, rn, ctr, li, Bp, dev, s, words_only); break;
+            default: run_stage<256, W>(par, w, st, tsph, o, rn, ctr, li, Bp, dev, s, words_only); break;
         }
     };
-    stage(top, 0u, pairs_of(L), w.runs[L - 1], (int)L - 1, 0u, std::false_type{});
+    const bool words = tp->level1_words != 0 && L >= 2;
+    out->words = crsh_pair_words{};
+    stage(top, 0u, pairs_of(L), w.runs[L - 1], (int)L - 1, 0u, std::false_type{}, false);
     // levels L-1 .. 1: parents are the nodes of level l+1 and their pair runs
     for (unsigned l = L - 1; l >= 1; --l) {
         PairOut par = pairs_of(l + 1);
         LevelParents lp{par.tri, w.runs[l].start, w.runs[l].end, h->count + l, h->count + (l - 1), level_nodes(l), logB};
+        const bool wo = words && l == 1;
         if (B > 32)
-            stage(lp, L - l, pairs_of(l), w.runs[l - 1], (int)l - 1, B, std::true_type{});
+            stage(lp, L - l, pairs_of(l), w.runs[l - 1], (int)l - 1, B, std::true_type{}, wo);
         else
-            stage(lp, L - l, pairs_of(l), w.runs[l - 1], (int)l - 1, B, std::false_type{});
+            stage(lp, L - l, pairs_of(l), w.runs[l - 1], (int)l - 1, B, std::false_type{}, wo);
+        if (wo) {   // level 1 stays in the ballots of its count pass
+            out->words = crsh_pair_words{w.sb.mask, par.tri, reinterpret_cast<const uint32_t*>(w.items),
+                                         w.sb.totals + 2, 1u, 0u};
+        }
         if (l == 1) break;
     }
-    {
+    if (!words) {
         const unsigned blocks = (h->capacity[0] + 256) / 256;
         launch_pdl(k_runs_to_csr, std::min<unsigned>(blocks, dev.sms * 8), 256, 0, s, w.runs[0], out->node,
                    (const unsigned*)h->count, (const unsigned*)out->count, cap, out->node_offsets);

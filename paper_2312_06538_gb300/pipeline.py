@@ -45,10 +45,14 @@ class Pipeline:
     """Buffers for one scene and up to `ray_capacity` rays; run() issues the path on a stream."""
 
     def __init__(self, scene, *, max_pixels: int, n_lights: int, bundle: int, levels: int,
-                 ray_capacity: Optional[int] = None, pair_capacity: Optional[int] = None, device="cuda"):
+                 ray_capacity: Optional[int] = None, pair_capacity: Optional[int] = None, device="cuda",
+                 level1_words: bool = False):
         C.load()
         self.device = torch.device(device)
         self.bundle, self.levels = int(bundle), int(levels)
+        # level 1 in word form: crsh_traverse leaves it in its ballots and crsh_closest_hit reads them
+        # there (no level-1 pair list; hierarchies of two or more levels)
+        self.level1_words = bool(level1_words) and self.levels >= 2
         dev = self.device
         f32, u32 = torch.float32, torch.int32
         # scene
@@ -159,8 +163,10 @@ class Pipeline:
     def build(self, bp: C.crsh_build_params, stream: int):
         C.crsh_build(self.rays, _ptr(self.n_rays), bp, self.hier, stream)
 
-    def traverse(self, mesh_cull: bool, stream: int, block_threads: int = 0):
-        C.crsh_traverse(self.hier, self.scene, C.crsh_traverse_params(int(bool(mesh_cull)), int(block_threads)),
+    def traverse(self, mesh_cull: bool, stream: int, block_threads: int = 0, words: Optional[bool] = None):
+        words = self.level1_words if words is None else bool(words)
+        C.crsh_traverse(self.hier, self.scene,
+                        C.crsh_traverse_params(int(bool(mesh_cull)), int(block_threads), int(words)),
                         self.pairs, _ptr(self.counters), _ptr(self.ws_trav), self.ws_trav_bytes, stream)
 
     def closest_hit(self, stream: int, hits: Optional[C.crsh_hits] = None):
@@ -292,15 +298,17 @@ class Pipeline:
                  self.trig[l][:cnt[l]].cpu().numpy()) for l in range(self.levels)]
 
     def pairs_host(self):
+        if self.pairs.words.valid:
+            raise RuntimeError("level 1 is in word form: no pair list was written")
         p = min(int(self.pair_count.item()), self.pair_capacity)
         cnt = int(self.level_count[0].item())
         return (self.pair_node[:p].cpu().numpy().view(np.uint32), self.pair_tri[:p].cpu().numpy().view(np.uint32),
                 self.pair_off[:cnt + 1].cpu().numpy().view(np.uint32))
 
 
-def workload_pipeline(w, *, device="cuda", pair_capacity=None) -> "Pipeline":
+def workload_pipeline(w, *, device="cuda", pair_capacity=None, level1_words=False) -> "Pipeline":
     return Pipeline(w.scene, max_pixels=w.n_pixels, n_lights=w.lights.shape[0], bundle=w.bundle, levels=w.levels,
-                    pair_capacity=pair_capacity, device=device)
+                    pair_capacity=pair_capacity, device=device, level1_words=level1_words)
 
 
 def workload_params(w, *, sort=True, compress=True):

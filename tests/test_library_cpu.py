@@ -50,7 +50,7 @@ def test_version_and_status_strings():
 
 STRUCTS = ["crsh_gbuffer", "crsh_rays_in", "crsh_hash_params", "crsh_rays", "crsh_counters", "crsh_scene",
            "crsh_build_params", "crsh_hierarchy", "crsh_traverse_params", "crsh_pairs", "crsh_hits", "crsh_camera",
-           "crsh_gbuffer_out", "crsh_scene_out"]
+           "crsh_gbuffer_out", "crsh_scene_out", "crsh_pair_words"]
 
 
 def test_ctypes_layout_matches_header():
