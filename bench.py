@@ -284,12 +284,12 @@ def run_reference(args, w):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def closest_traffic():
-    """DRAM bytes per k_closest launch from the committed ncu summary, or None when
-    the kernel source changed since those counters were taken."""
+def closest_traffic(kernel: str = "k_closest"):
+    """DRAM bytes per launch of the final-test kernel from the committed ncu summary, or None
+    when the kernel source changed since those counters were taken."""
     import hashlib
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_closest"]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
             return None
@@ -435,10 +435,12 @@ def batched_comparison(dev, n_batches=32, reps=5):
     tune_s = time.perf_counter() - t0
     plain = bt.PlainBatches(batches, pads_of, hp_of, device=dev)
     plain_g = bt.PlainBatches(batches, pads_of, hp_of, device=dev)
+    plain_w = bt.PlainBatches(batches, pads_of, hp_of, device=dev, level1_words=True)
     fixed = bt.BatchedCRSH(batches, pads_of, hp_of, tuner=bt.Autotuner(bundles=(16,), depths=(4,), reps=1, blocks=(256,)),
                            n_streams=8, device=dev)
     bat.capture()
     plain_g.capture()
+    plain_w.capture()
     fixed.capture()
     total = sum(n for _, _, n in batches)
     stream = torch.cuda.current_stream(dev)
@@ -459,10 +461,11 @@ def batched_comparison(dev, n_batches=32, reps=5):
         return sorted(ts)[len(ts) // 2]
     tp = timed(plain.run)
     tpg = timed(plain_g.replay)
+    tpw = timed(plain_w.replay)
     tf = timed(fixed.replay)
     tb = timed(bat.replay)
     identical = all(torch.equal(x.view(torch.int32), y.view(torch.int32))
-                    for runs in (bat.runs, plain_g.runs, fixed.runs)
+                    for runs in (bat.runs, plain_g.runs, plain_w.runs, fixed.runs)
                     for a, b in zip(runs, plain.runs) for x, y in zip(a.hits(), b.hits()))
     out = {"workload": f"{len(batches)} batches, {total:,} rays, sizes {min(n for n, _ in spec)}..{max(n for n, _ in spec)}, "
                        f"8 scenes of 5k..200k triangles",
@@ -472,11 +475,13 @@ def batched_comparison(dev, n_batches=32, reps=5):
            "ablation": {
                "plain_eager_ms": 1e3 * tp,
                "plain_one_graph_one_stream_ms": 1e3 * tpg,
+               "plain_words_one_graph_one_stream_ms": 1e3 * tpw,
                "untuned_B16_L4_graph_8_streams_ms": 1e3 * tf,
                "tuned_graph_8_streams_ms": 1e3 * tb,
-               "what": "plain calls issued from Python on one stream; the same calls captured in one graph on "
-                       "one stream (removes host launch gaps); every batch at B=16, L=4 in one graph over 8 "
-                       "streams (adds concurrency); the autotuned B, L in that graph (adds tuning)"},
+               "what": "plain calls issued from Python on one stream (level 1 as a list); the same calls "
+                       "captured in one graph on one stream (removes host launch gaps); the same with level 1 "
+                       "in word form (adds the word form); every batch at B=16, L=4 in one graph over 8 streams "
+                       "(adds concurrency); the autotuned B, L, block in that graph (adds tuning)"},
            "timing": "CUDA events on the launching stream, median of reps",
            "tuned": {str(k): list(v) for k, v in sorted(tuner.table.items())},
            "prep_s": prep_s, "tune_s": tune_s}
@@ -808,7 +813,7 @@ def run_gpu(args, w):
     achieved = c["final_tests"] * MT_FLOPS / (ch_ms * 1e-3) / 1e12
     tr_ms = float(stage[:, 2].mean())
     eq9_tests = sum(c["tests"]) + c["mesh_tests"]
-    traffic = closest_traffic()
+    traffic = closest_traffic("k_closest_words" if p.level1_words else "k_closest")
     words = bool(p.level1_words)
     roofline = {"kernel": ("crsh_closest_hit (k_closest_words: level-1 ballots gathered into groups, then tested; "
                            "+ fill + finalize)") if words else "crsh_closest_hit (k_closest + fill + finalize)",

@@ -58,11 +58,11 @@ class BatchRun:
     """Buffers and calls for one batch of prebuilt rays with a given hierarchy shape."""
 
     def __init__(self, scene, rays: Dict[str, torch.Tensor], n: int, bundle: int, levels: int, pads, hp,
-                 device="cuda", block: int = 256):
+                 device="cuda", block: int = 256, level1_words: bool = True):
         self.n = n
         self.rays = rays
         self.p = Pipeline(scene, max_pixels=0, n_lights=0, bundle=bundle, levels=levels, ray_capacity=max(1, n),
-                          pair_capacity=max(1 << 16, 32 * n), device=device)
+                          pair_capacity=max(1 << 16, 32 * n), device=device, level1_words=level1_words)
         self.rin = Pipeline.rays_in_struct(rays)
         self.hp = hp
         self.bp = build_params(bundle, levels, pads)
@@ -199,15 +199,17 @@ class BatchedCRSH:
 
 
 class PlainBatches:
-    """Reference: each batch through the four calls in turn, default B = 16, L = 4, one stream.
+    """Reference: each batch through the four calls in turn, default B = 16, L = 4, level 1 as a
+    list, one stream.
     capture() records the same calls, in the same order on one stream, as one CUDA graph
     (the ablation that removes only the host's launch gaps)."""
 
-    def __init__(self, batches, pads_of, hp_of, device="cuda", bundle=16, levels=4):
+    def __init__(self, batches, pads_of, hp_of, device="cuda", bundle=16, levels=4, level1_words=False):
         self.device = torch.device(device)
         self.runs = []
         for scene, rays, n in batches:
-            br = BatchRun(scene, rays, n, bundle, levels, pads_of(scene), hp_of(scene), device)
+            br = BatchRun(scene, rays, n, bundle, levels, pads_of(scene), hp_of(scene), device,
+                          level1_words=level1_words)
             br.fit()
             self.runs.append(br)
         self.graph = None
