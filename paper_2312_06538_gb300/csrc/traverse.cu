@@ -773,11 +773,12 @@ __global__ void k_items(LevelParents par, StageBuf sb, uint4* items) {
         const unsigned first = p << par.logB;
         const unsigned nc = first >= cc ? 0u : min(1u << par.logB, cc - first);
         const unsigned ob = sb.obase[p], ib = sb.ibase[p];
-        for (unsigned c = 0; c < nc; ++c)
-            for (unsigned g = lane; g < nseg; g += 32) {
-                const unsigned k = g * WORD_SEG;
-                items[ib + c * nseg + g] = make_uint4(first + c, s + 32 * k, ob + c * nch + k, min(WORD_SEG, nch - k));
-            }
+        // item j = c * nseg + g of the parent: consecutive lanes write consecutive descriptors
+        for (unsigned j = lane; j < nc * nseg; j += 32) {
+            const unsigned c = j / nseg, g = j - c * nseg;
+            const unsigned k = g * WORD_SEG;
+            items[ib + j] = make_uint4(first + c, s + 32 * k, ob + c * nch + k, min(WORD_SEG, nch - k));
+        }
     }
 }
 
