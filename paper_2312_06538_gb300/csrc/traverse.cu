@@ -487,90 +487,95 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
         unsigned p, wo, len;
     };
     auto slot_of = [&]() { return Slot{lead.c.p, lead.c.ob + (lead.u - lead.c.ub), lead.c.len}; };
-    Slot s0 = slot_of();
-    bool v0, v1 = false;
-    float4 ts0 = zero;
-    {
-        const unsigned t0 = lead.c.tri(par, lead.u, v0);
-        if (v0) ts0 = tri_sphere[t0];
-    }
-    bool has1 = lead.step(par, sb, ws, claim);
-    Slot s1 = s0;
-    unsigned t1 = 0;
-    if (has1) {
-        s1 = slot_of();
-        t1 = lead.c.tri(par, lead.u, v1);
-    }
     // the tested unit's parent: its children (set when the parent changes)
     unsigned cur_p = 0xffffffffu, nc = 0;
     unsigned long long accepted = 0;   // pairs accepted by this warp (word form's level count)
     const float4* csp = s_sp[warp];
     const float4* cco = s_co[warp];
     const float2* ctg = s_tg[warp];
-    for (;;) {
-        float4 ts1 = zero;
-        if (v1) ts1 = tri_sphere[t1];
-        Slot s2 = s1;
-        bool has2 = false, v2 = false;
-        unsigned t2 = 0;
-        if (has1) {
-            has2 = lead.step(par, sb, ws, claim);
-            if (has2) {
-                s2 = slot_of();
-                t2 = lead.c.tri(par, lead.u, v2);
-            }
-        }
-        if (s0.p != cur_p) {   // warp-uniform
-            cur_p = s0.p;
-            nc = par.nchild(cur_p);
-            const unsigned a0 = par.child_id(cur_p, 0);
-            __syncwarp();      // the previous parent's children are no longer read
-            for (unsigned cl = lane; cl < nc; cl += 32) {
-                s_sp[warp][cl] = par.child.sphere[a0 + cl];
-                s_co[warp][cl] = par.child.cone[a0 + cl];
-                s_tg[warp][cl] = par.child.trig[a0 + cl];
-            }
-            __syncwarp();
-        }
-        const unsigned nch = (s0.len + 31) >> 5;
-        unsigned* mw = sb.mask + s0.wo;
-        if (Parents::kChunkCull) {
-            const float4 K = chunk_sphere(ts0, v0);
-            // children in groups of 32 (lane = child); more than one group only when B = 64
-#pragma unroll
-            for (unsigned cb = 0; cb < (WIDE ? 64u : 32u); cb += 32) {
-                const unsigned cl = cb + lane;
-                const bool mine = cl < nc;
-                const bool acc = mine && eq9(csp[cl], cco[cl], ctg[cl], K);
-                if (mine && !acc) mw[cl * nch] = 0u;
-                unsigned todo = __ballot_sync(FULL, acc);
-                while (todo) {
-                    const unsigned c = cb + __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
-                    const unsigned m = __ballot_sync(FULL, ok);
-                    if (lane == 0) mw[c * nch] = m;
-                    accepted += __popc(m);
-                }
-            }
-        } else {
-#pragma unroll 4
-            for (unsigned c = 0; c < nc; ++c) {
-                const bool ok = v0 & eq9(csp[c], cco[c], ctg[c], ts0);
-                const unsigned m = __ballot_sync(FULL, ok);
-                if (lane == 0) mw[c * nch] = m;
-                accepted += __popc(m);
-            }
-        }
-        if (!has1) break;
-        s0 = s1;
-        v0 = v1;
-        ts0 = ts1;
-        s1 = s2;
-        has1 = has2;
-        v1 = v2;
-        t1 = t2;
+    // three units in flight in rotating slot sets A, B, C: the loop is unrolled three times so
+    // that no slot is copied (STEP(X, Y, Z): test unit X, fetch unit Y's sphere, unit Z's index)
+    Slot sA = slot_of(), sB = sA, sC = sA;
+    bool vA = false, vB = false, vC = false, hB = false, hC = false;
+    float4 tsA = zero, tsB = zero, tsC = zero;
+    unsigned tB = 0, tC = 0;
+    {
+        const unsigned t0 = lead.c.tri(par, lead.u, vA);
+        tsA = tri_sphere[vA ? t0 : 0u];
     }
+    hB = lead.step(par, sb, ws, claim);
+    if (hB) {
+        sB = slot_of();
+        tB = lead.c.tri(par, lead.u, vB);
+    }
+    (void)tsC; (void)tC; (void)hC; (void)vC;
+#define CRSH_TEST_UNIT(S0, V0, TS0)                                                          \
+    {                                                                                        \
+        if (S0.p != cur_p) {                                                                 \
+            cur_p = S0.p;                                                                    \
+            nc = par.nchild(cur_p);                                                          \
+            const unsigned a0 = par.child_id(cur_p, 0);                                      \
+            __syncwarp();                                                                    \
+            for (unsigned cl = lane; cl < nc; cl += 32) {                                    \
+                s_sp[warp][cl] = par.child.sphere[a0 + cl];                                  \
+                s_co[warp][cl] = par.child.cone[a0 + cl];                                    \
+                s_tg[warp][cl] = par.child.trig[a0 + cl];                                    \
+            }                                                                                \
+            __syncwarp();                                                                    \
+        }                                                                                    \
+        const unsigned nch = (S0.len + 31) >> 5;                                             \
+        unsigned* mw = sb.mask + S0.wo;                                                      \
+        if (Parents::kChunkCull) {                                                           \
+            const float4 K = chunk_sphere(TS0, V0);                                          \
+            _Pragma("unroll") for (unsigned cb = 0; cb < (WIDE ? 64u : 32u); cb += 32) {     \
+                const unsigned cl = cb + lane;                                               \
+                const bool mine = cl < nc;                                                   \
+                const bool acc = mine && eq9(csp[cl], cco[cl], ctg[cl], K);                  \
+                if (mine && !acc) mw[cl * nch] = 0u;                                         \
+                unsigned todo = __ballot_sync(FULL, acc);                                    \
+                while (todo) {                                                               \
+                    const unsigned c = cb + __ffs(todo) - 1;                                 \
+                    todo &= todo - 1;                                                        \
+                    const bool ok = V0 & eq9(csp[c], cco[c], ctg[c], TS0);                   \
+                    const unsigned m = __ballot_sync(FULL, ok);                              \
+                    mw[c * nch] = m;                                                         \
+                    accepted += __popc(m);                                                   \
+                }                                                                            \
+            }                                                                                \
+        } else {                                                                             \
+            _Pragma("unroll 4") for (unsigned c = 0; c < nc; ++c) {                          \
+                const bool ok = V0 & eq9(csp[c], cco[c], ctg[c], TS0);                       \
+                const unsigned m = __ballot_sync(FULL, ok);                                  \
+                mw[c * nch] = m;                                                             \
+                accepted += __popc(m);                                                       \
+            }                                                                                \
+        }                                                                                    \
+    }
+#define CRSH_COUNT_STEP(X, Y, Z)                                                             \
+    {                                                                                        \
+        ts##Y = tri_sphere[v##Y ? t##Y : 0u];                                                \
+        h##Z = false;                                                                        \
+        v##Z = false;                                                                        \
+        t##Z = 0;                                                                            \
+        if (h##Y) {                                                                          \
+            h##Z = lead.step(par, sb, ws, claim);                                            \
+            if (h##Z) {                                                                      \
+                s##Z = slot_of();                                                            \
+                t##Z = lead.c.tri(par, lead.u, v##Z);                                        \
+            }                                                                                \
+        }                                                                                    \
+        CRSH_TEST_UNIT(s##X, v##X, ts##X)                                                    \
+        if (!h##Y) break;                                                                    \
+    }
+    bool hA = false;
+    unsigned tA = 0;
+    for (;;) {
+        CRSH_COUNT_STEP(A, B, C)
+        CRSH_COUNT_STEP(B, C, A)
+        CRSH_COUNT_STEP(C, A, B)
+    }
+#undef CRSH_COUNT_STEP
+#undef CRSH_TEST_UNIT
     if (popsum && lane == 0 && accepted) atomicAdd(popsum, accepted);
 }
 
@@ -738,7 +743,11 @@ __global__ void __launch_bounds__(BLK) k_emit(Parents par, StageBuf sb, PairOut 
                 any &= any - 1;
                 const unsigned m = __shfl_sync(FULL, l0.mc[g], c);
                 const unsigned base = __shfl_sync(FULL, l0.pc[g], c);
-                if ((m >> lane) & 1u) store_pair(out, base + __popc(m & lt), par.child_id(c0.p, 32 * g + c), l0.t);
+                // predicated stores (no branch): this lane's bit, inside the list's capacity
+                const unsigned long long pos = base + __popc(m & lt);
+                const bool wr = ((m >> lane) & 1u) && pos < out.cap;
+                if (wr) out.tri[pos] = l0.t;
+                if (out.node && wr) out.node[pos] = par.child_id(c0.p, 32 * g + c);
             }
             const unsigned cl = 32u * g + lane;
             if (ch == 0 && cl < nc) {
