@@ -24,11 +24,12 @@ def _frames(w, n):
     return out
 
 
-def test_frames_match_direct_runs_bitwise():
+@pytest.mark.parametrize("words", [False, True])
+def test_frames_match_direct_runs_bitwise(words):
     from paper_2312_06538_gb300 import frames as fr
     from paper_2312_06538_gb300 import pipeline as pl
     w = synthetic.make(2, res=96)
-    p = pl.workload_pipeline(w)
+    p = pl.workload_pipeline(w, level1_words=words)
     hp, bp = pl.workload_params(w)
     frames = _frames(w, 5)
     refs = []
