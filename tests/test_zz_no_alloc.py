@@ -12,11 +12,11 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _pipeline():
+def _pipeline(words=False):
     import synthetic
     from paper_2312_06538_gb300 import pipeline as pl
     w = synthetic.make(2, res=96)
-    p = pl.workload_pipeline(w)
+    p = pl.workload_pipeline(w, level1_words=words)
     hp, bp = pl.workload_params(w)
     g = p.gbuffer_struct(p.gbuffer_to_device(w.gbuffer))
     lights = torch.from_numpy(w.lights).cuda()
@@ -24,9 +24,11 @@ def _pipeline():
     return p, c
 
 
-def test_noalloc_matches_workspace_call_twice_in_a_row():
+@pytest.mark.parametrize("words", [False, True])
+def test_noalloc_matches_workspace_call_twice_in_a_row(words):
     from paper_2312_06538_gb300 import crsh as C
-    p, c = _pipeline()
+    p, c = _pipeline(words)
+    assert bool(p.pairs.words.valid) == words
     ref = [x.copy() for x in p.hits_host()]
     assert (ref[0] >= 0).sum() > 0
     stream = torch.cuda.current_stream().cuda_stream
