@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest(const uint32_t* pnode, 
 // records copied while the current one is tested, and each item's words are
 // loaded while the item before it is gathered.
 // ---------------------------------------------------------------------------
-constexpr unsigned WI_BATCH = 8;   // work items per claim (at most 32)
+constexpr unsigned WI_BATCH = 4;   // work items per claim at most (of 2, 3, 4, 6, 8, 16: 4 measured best)
 
 template <int B>
 __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest_words(crsh_pair_words pw, RaysDev rays,
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest_words(crsh_pair_words p
     unsigned long long n_tests = 0, n_hits = 0;
     // ---- producer: items -> words -> triangle ids -> groups (warp-uniform but the per-lane values) ----
     // batches of items from the counter: lane 0 holds the next one (start, size), claimed one
-    // batch ahead; sizes shrink toward the end (about a quarter of the items left per warp)
+    // batch ahead; sizes shrink toward the end (about a sixteenth of the items left per warp)
     unsigned cl_base = 0, cl_size = WI_BATCH;
     if (lane == 0) cl_base = atomicAdd(work, WI_BATCH);
     uint4 desc = make_uint4(0, 0, 0, 0);       // lane j < nb: item j of the batch
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest_words(crsh_pair_words p
         if (base >= I) return false;
         if (lane == 0) {
             const unsigned done = base + size, left = done < I ? I - done : 0u;
-            cl_size = max(1u, min(WI_BATCH, left / (4u * nw)));
+            cl_size = max(1u, min(WI_BATCH, left / (16u * nw)));
             cl_base = atomicAdd(work, cl_size);
         }
         nb = min(size, I - base);
