@@ -179,12 +179,13 @@ def test_bundle_and_depth(B, L):
     parity.check_report(rep)
 
 
-def test_empty_and_tiny_inputs():
+@pytest.mark.parametrize("words", [False, True])
+def test_empty_and_tiny_inputs(words):
     from paper_2312_06538_gb300 import pipeline as pl
     w = synthetic.make(2, res=16)
     g = {k: v.copy() for k, v in w.gbuffer.items()}
     g["hit"][:] = 0
-    p = pl.workload_pipeline(w)
+    p = pl.workload_pipeline(w, level1_words=words)
     hp, bp = pl.workload_params(w)
     lights = torch.from_numpy(w.lights).cuda()
     c = p.run_fit(p.gbuffer_struct(p.gbuffer_to_device(g)), lights, hp, bp)
