@@ -368,6 +368,13 @@ struct UnitCursor {
         valid = j < len;
         return valid ? par.tri(s, j) : 0u;
     }
+    // the same with an in-range load for every lane (the run is not empty); the
+    // caller masks the lanes that are not valid
+    __device__ __forceinline__ unsigned tri_any(const Parents& par, unsigned u, bool& valid) const {
+        const unsigned j = ((u - ub) << 5) + (threadIdx.x & 31);
+        valid = j < len;
+        return par.tri(s, valid ? j : 0u);
+    }
 };
 
 // Work split of a count or emit pass.  With at least dyn_min units per warp
@@ -500,13 +507,13 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
     float4 tsA = zero, tsB = zero, tsC = zero;
     unsigned tB = 0, tC = 0;
     {
-        const unsigned t0 = lead.c.tri(par, lead.u, vA);
+        const unsigned t0 = lead.c.tri_any(par, lead.u, vA);
         tsA = tri_sphere[vA ? t0 : 0u];
     }
     hB = lead.step(par, sb, ws, claim);
     if (hB) {
         sB = slot_of();
-        tB = lead.c.tri(par, lead.u, vB);
+        tB = lead.c.tri_any(par, lead.u, vB);
     }
     (void)tsC; (void)tC; (void)hC; (void)vC;
 #define CRSH_TEST_UNIT(S0, V0, TS0)                                                          \
@@ -530,7 +537,7 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
             _Pragma("unroll") for (unsigned cb = 0; cb < (WIDE ? 64u : 32u); cb += 32) {     \
                 const unsigned cl = cb + lane;                                               \
                 const bool mine = cl < nc;                                                   \
-                const bool acc = mine && eq9(csp[cl], cco[cl], ctg[cl], K);                  \
+                const bool acc = WIDE ? (mine && eq9(csp[cl], cco[cl], ctg[cl], K)) : (mine & eq9(csp[cl], cco[cl], ctg[cl], K));                  \
                 if (mine && !acc) mw[cl * nch] = 0u;                                         \
                 unsigned todo = __ballot_sync(FULL, acc);                                    \
                 while (todo) {                                                               \
@@ -561,7 +568,7 @@ __global__ void __launch_bounds__(BLK, 1024 / BLK) k_count(Parents par, StageBuf
             h##Z = lead.step(par, sb, ws, claim);                                            \
             if (h##Z) {                                                                      \
                 s##Z = slot_of();                                                            \
-                t##Z = lead.c.tri(par, lead.u, v##Z);                                        \
+                t##Z = lead.c.tri_any(par, lead.u, v##Z);                                        \
             }                                                                                \
         }                                                                                    \
         CRSH_TEST_UNIT(s##X, v##X, ts##X)                                                    \
