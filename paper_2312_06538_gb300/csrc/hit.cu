@@ -18,7 +18,9 @@
 // triangle and scatters hits to the rays' generation order.  Decisions
 // (which triangle is closest) are FP32; the reported (t, u, v) of the winner
 // are recomputed in double-word (float + float) arithmetic from the FP32
-// inputs.
+// inputs.  With level 1 in word form (crsh_pair_words) the groups are gathered
+// from the traversal's ballots instead (k_closest_words) and run the same
+// group test.
 #include <atomic>
 #include <mutex>
 

@@ -13,7 +13,11 @@
 //               No per-element division, no chains of dependent loads, no
 //               waits between blocks.
 // The emit pass also records each child's run [start, end) of the output,
-// which is how the next level finds a parent's triangles.
+// which is how the next level finds a parent's triangles.  In word form
+// (crsh_traverse_params.level1_words) the last stage stops after its count
+// pass: its ballots, with one work-item descriptor per (parent, child,
+// segment of WORD_SEG chunks) written by k_items, are level 1's candidates,
+// read by the final tests in place.
 #include <algorithm>
 #include <atomic>
 #include <type_traits>
