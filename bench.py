@@ -23,6 +23,7 @@ import subprocess
 import sys
 import threading
 import time
+from typing import Optional
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -284,12 +285,15 @@ def run_reference(args, w):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def closest_traffic(kernel: str = "k_closest"):
+def closest_traffic(kernel: str, config: int, res) -> Optional[float]:
     """DRAM bytes per launch of the final-test kernel from the committed ncu summary, or None
-    when the kernel source changed since those counters were taken."""
+    when the record is of another workload or the kernel source changed since those counters
+    were taken."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        if rec["config"] != config or res is not None:
+            return None
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
             return None
@@ -813,7 +817,7 @@ def run_gpu(args, w):
     achieved = c["final_tests"] * MT_FLOPS / (ch_ms * 1e-3) / 1e12
     tr_ms = float(stage[:, 2].mean())
     eq9_tests = sum(c["tests"]) + c["mesh_tests"]
-    traffic = closest_traffic("k_closest_words" if p.level1_words else "k_closest")
+    traffic = closest_traffic("k_closest_words" if p.level1_words else "k_closest", args.config, args.res)
     words = bool(p.level1_words)
     roofline = {"kernel": ("crsh_closest_hit (k_closest_words: level-1 ballots gathered into groups, then tested; "
                            "+ fill + finalize)") if words else "crsh_closest_hit (k_closest + fill + finalize)",
