@@ -468,9 +468,26 @@ __global__ void k_prepare(crsh_scene sc) {
         mt[0] = make_float4(a.x, a.y, a.z, n.x);
         mt[1] = make_float4(e1.x, e1.y, e1.z, n.y);
         mt[2] = make_float4(e2.x, e2.y, e2.z, n.z);
-        // pre-test radius of the final tests, squared: 1.1 r^2 (with the
-        // grazing slack of the test, (a + b)^2 <= 1.1 a^2 + 11 b^2)
-        mt[3] = make_float4(m.x, m.y, m.z, 1.1f * r * r);
+        // the final tests' pre-test sphere: the tightest of the spheres about the
+        // centroid, the three edge midpoints and the circumcentre that hold all three
+        // vertices (the smallest enclosing sphere is centred at one of the last four);
+        // its radius is measured from the chosen centre, so any centre is safe, and
+        // padded as above.  Squared and scaled: 1.05 r^2 (with the grazing slack of
+        // the test, (a + b)^2 <= 1.05 a^2 + 21 b^2)
+        f3 pc = m;
+        float pr = fmaxf(len(a - m), fmaxf(len(b - m), len(c - m)));
+        auto consider = [&](f3 x) {
+            const float rx = fmaxf(len(a - x), fmaxf(len(b - x), len(c - x)));
+            if (rx < pr) { pr = rx; pc = x; }   // a NaN centre (degenerate triangle) is never taken
+        };
+        consider((a + b) * 0.5f);
+        consider((b + c) * 0.5f);
+        consider((a + c) * 0.5f);
+        const float nn = dot(n, n);
+        consider(a + (cross(n, e1) * dot(e2, e2) + cross(e2, n) * dot(e1, e1)) * (0.5f / nn));
+        const float pmag = fabsf(pc.x) + fabsf(pc.y) + fabsf(pc.z) + pr;
+        pr = pr * (1.0f + 9.6e-7f) + 3.9e-6f * pmag;
+        mt[3] = make_float4(pc.x, pc.y, pc.z, 1.05f * pr * pr);
     }
 }
 

@@ -67,10 +67,10 @@ __device__ __forceinline__ unsigned long long hit_key(float t, unsigned tri) {
 // Pre-test of a final test: a ray can only hit a triangle if its line passes
 // through the triangle's bounding sphere.  With v = c - o and s = v.d, the
 // squared distance from the centre to the line is |v|^2 - s^2 / |d|^2;
-// accept iff |v|^2 <= q + (1 + K) s^2 / |d|^2 with q = 1.1 r^2 and K = 2e-6.
+// accept iff |v|^2 <= q + (1 + K) s^2 / |d|^2 with q = 1.05 r^2 and K = 2e-6.
 // Whenever the line passes within r + 1e-4 x the distance along the ray (a
 // slack far above the FP32 error of Moller-Trumbore's hit point, even at
-// grazing incidence; (a + b)^2 <= 1.1 a^2 + 11 b^2) this holds with room for
+// grazing incidence; (a + b)^2 <= 1.05 a^2 + 21 b^2) this holds with room for
 // the FP32 rounding of |v|^2 and s^2 (a few ulps of |v|^2), so every
 // triangle Moller-Trumbore would hit passes.  The brute force takes the same
 // pre-test, so both paths decide hits with one function.
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(CH_BLOCK, 8) k_closest(const uint32_t* pnode, 
 constexpr unsigned WI_BATCH = 4;   // work items per claim at most (of 2, 3, 4, 6, 8, 16: 4 measured best)
 
 template <int B>
-__global__ void __launch_bounds__(CH_BLOCK, 8) k_closest_words(crsh_pair_words pw, RaysDev rays,
+__global__ void __launch_bounds__(CH_BLOCK, 7) k_closest_words(crsh_pair_words pw, RaysDev rays,
                                                                const unsigned* n_ptr, unsigned n_cap,
                                                                const float4* tri_mt, unsigned long long* best,
                                                                unsigned* work, crsh_counters* ctr) {
