@@ -304,13 +304,13 @@ def closest_traffic(kernel: str, config: int, res) -> Optional[float]:
 
 def launches_per_step(levels: int, compress: bool, words: bool = False) -> int:
     """Kernels of libcrsh.so launched by one pass (count of <<<>>> in the call sequence)."""
-    # tables, gen, chunk (which also counts the digits) or hist, plan, 4 passes, pos, gather
-    hash_sort = 1 + 1 + 1 + 1 + 4 + (1 if compress else 0) + 1
+    # tables, zeroing, gen, chunk (which also counts the digits) or hist, plan, 4 passes, pos, gather
+    hash_sort = 1 + 1 + 1 + 1 + 1 + 4 + (1 if compress else 0) + 1
     build = max(1, levels - 1)   # level 1 (with level 2 merged in), then one per level above
-    if words and levels >= 2:    # mesh stage, top stage, 5 kernels per level above 1; unit scan, count, items at 1
-        traverse = 1 + 5 + 5 * (levels - 2) + 3
-    else:                        # mesh stage, top stage, 5 kernels per level, csr
-        traverse = 1 + 5 + 5 * (levels - 1) + 1
+    if words and levels >= 2:    # zeroing, mesh stage, top stage, 5 kernels per level above 1; unit scan, count, items at 1
+        traverse = 1 + 1 + 5 + 5 * (levels - 2) + 3
+    else:                        # zeroing, mesh stage, top stage, 5 kernels per level, csr
+        traverse = 1 + 1 + 5 + 5 * (levels - 1) + 1
     closest = 3
     return hash_sort + build + traverse + closest
 

@@ -332,6 +332,27 @@ __global__ void k_gen_rays(crsh_rays_in in, HashDev h, GenOut out, unsigned* n_o
     }
 }
 
+// Zeroing of the ranges of a ZeroSpans: 16-byte stores over each range's
+// aligned middle, 4-byte stores at its ends.
+__global__ void k_zero(ZeroSpans z) {
+    pdl_wait();
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        char* p = static_cast<char*>(z.p[r]);
+        const size_t n = p ? z.bytes[r] : 0;
+        const size_t head = min(n, (size_t)((16u - ((uintptr_t)p & 15u)) & 15u));
+        const size_t n16 = (n - head) / 16, tail = head + 16 * n16;
+        for (size_t i = tid; i < head / 4; i += nt) reinterpret_cast<unsigned*>(p)[i] = 0u;
+        for (size_t i = tid; i < n16; i += nt) reinterpret_cast<uint4*>(p + head)[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (size_t i = tid; i < (n - tail) / 4; i += nt) reinterpret_cast<unsigned*>(p + tail)[i] = 0u;
+    }
+}
+
+void zero_launch(const ZeroSpans& z, cudaStream_t s, const DeviceInfo& dev) {
+    launch_pdl(k_zero, dev.sms * 4, 256, 0, s, z);
+}
+
 // Threshold tables of the bins: cos(k pi / B) for k < B and tan(j (pi/4) / M)
 // for j < M, each evaluated in FP64 from the same FP64 argument expression as
 // the definition and rounded to FP32; one thread per entry.
@@ -940,9 +961,7 @@ crsh_status hash_sort_launch(const crsh_gbuffer* gb, const crsh_rays_in* in, con
     h.stb = hp->shadow_theta_bits; h.spb = hp->shadow_phi_bits;
     h.cb = hp->sec_cell_bits; h.tb = hp->sec_theta_bits; h.pb = hp->sec_phi_bits;
 
-    if (cudaMemsetAsync(w.ctl_begin, 0, w.ctl_bytes, s) != cudaSuccess) return CRSH_ERR_CUDA;
-    if (cudaMemsetAsync(ctr, 0, sizeof(crsh_counters), s) != cudaSuccess) return CRSH_ERR_CUDA;
-    if (cudaMemsetAsync(n_out, 0, sizeof(uint32_t), s) != cudaSuccess) return CRSH_ERR_CUDA;
+    zero_launch(ZeroSpans{{w.ctl_begin, ctr, n_out}, {w.ctl_bytes, sizeof(crsh_counters), sizeof(uint32_t)}}, s, dev);
 
     const int persist = dev.sms * 8;
     if (gb) {

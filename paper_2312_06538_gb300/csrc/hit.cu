@@ -602,6 +602,7 @@ __global__ void k_fill_best(unsigned long long* best, const unsigned* n_ptr, uns
     const unsigned n = min(*n_ptr, n_cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (work) *work = 0;
+        ctr->final_tests = ctr->final_tests_paper = ctr->final_hits = 0;   // this call's counters
         if (*n_ptr > n_cap) set_status(ctr, CRSH_ERR_CAPACITY);
     }
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) best[i] = NO_HIT;
@@ -789,10 +790,6 @@ crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, c
     if (ws_bytes < closest_hit_workspace(rays->capacity)) return CRSH_ERR_INVALID_ARG;
     unsigned long long* best = reinterpret_cast<unsigned long long*>(ws);
     unsigned* work = reinterpret_cast<unsigned*>(best + rays->capacity);   // in the 256 spare bytes
-    {
-        char* c0 = reinterpret_cast<char*>(&ctr->final_tests);
-        if (cudaMemsetAsync(c0, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) return CRSH_ERR_CUDA;
-    }
     const unsigned fb = dev.sms * 8;
     const unsigned cap = rays->capacity;
     launch_pdl(k_fill_best, fb, 256, 0, s, best, n_rays, cap, work, ctr);

@@ -20,6 +20,16 @@ struct DeviceInfo {
     int sms = 0;
 };
 
+// Up to three byte ranges zeroed by one kernel (hash_sort.cu) instead of memset
+// nodes, so that the zeroing chains with the launches around it by
+// programmatic dependent launch.  Each range starts on a 4-byte boundary and
+// spans a multiple of 4 bytes; a null range is skipped.
+struct ZeroSpans {
+    void* p[3];
+    size_t bytes[3];
+};
+void zero_launch(const ZeroSpans& z, cudaStream_t s, const DeviceInfo& dev);
+
 // Up to four bin threshold tables to fill (hash_sort.cu): entry k of table i
 // is cos(k pi / n[i]) or, when is_tan[i], tan(k (pi/4) / n[i]), in FP32.
 struct TableSpec {

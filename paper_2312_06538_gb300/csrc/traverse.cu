@@ -964,12 +964,11 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
     const uint64_t cap = out->capacity;
     if (ws_bytes < traverse_workspace(h, sc->n_tris, sc->n_meshes, cap)) return CRSH_ERR_INVALID_ARG;
     TvWs w = carve_tv(ws, h, sc->n_tris, sc->n_meshes, cap);
-    if (cudaMemsetAsync(w.ctl, 0, w.ctl_bytes, s) != cudaSuccess) return CRSH_ERR_CUDA;
-    {   // reset this call's counters: mesh_tests .. tests_paper, and needed_pairs
+    {   // the control region, and this call's counters: mesh_tests .. tests_paper, and needed_pairs
         char* c0 = reinterpret_cast<char*>(&ctr->mesh_tests);
         char* c1 = reinterpret_cast<char*>(&ctr->final_tests);
-        if (cudaMemsetAsync(c0, 0, (size_t)(c1 - c0), s) != cudaSuccess) return CRSH_ERR_CUDA;
-        if (cudaMemsetAsync(&ctr->needed_pairs, 0, sizeof(unsigned long long), s) != cudaSuccess) return CRSH_ERR_CUDA;
+        zero_launch(ZeroSpans{{w.ctl, c0, &ctr->needed_pairs}, {w.ctl_bytes, (size_t)(c1 - c0), sizeof(unsigned long long)}},
+                    s, dev);
     }
     auto level_nodes = [&](unsigned l) {   // l = 1..L
         return Node3{reinterpret_cast<const float4*>(h->sphere[l - 1]), reinterpret_cast<const float4*>(h->cone[l - 1]),
