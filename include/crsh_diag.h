@@ -39,6 +39,20 @@ crsh_status crsh_lookback_selftest(unsigned long long *status64, uint32_t *statu
                                    uint32_t aggregate, uint32_t spin_limit, unsigned long long *prefix_out,
                                    crsh_counters *counters, void *stream);
 
+/* crsh_closest_hit with its final-test kernel timed (measurement only): the
+ * same arguments, validation and results as crsh_closest_hit (include/crsh.h,
+ * Section 3.3.8), plus *kernel_ms (host) = the duration of the final-test
+ * kernel (k_closest, or k_closest_words for level 1 in word form), measured
+ * with two CUDA events recorded on `stream` immediately before and after that
+ * kernel's launch.  Synchronous: returns after the call has completed on
+ * `stream`.  Errors: those of crsh_closest_hit; CRSH_ERR_INVALID_ARG if
+ * kernel_ms is NULL; CRSH_ERR_CUDA if an event call or the synchronisation
+ * fails (*kernel_ms is then not written). */
+crsh_status crsh_closest_hit_timed(const crsh_hierarchy *h, const crsh_rays *rays, const uint32_t *n_rays,
+                                   const crsh_scene *scene, const crsh_pairs *pairs, crsh_hits *out,
+                                   crsh_counters *counters, void *workspace, size_t workspace_bytes,
+                                   float *kernel_ms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -133,6 +133,10 @@ SIGNATURES = [
       ctypes.POINTER(crsh_pairs), ctypes.POINTER(crsh_hits), P, P]),
     ("crsh_bruteforce_closest_hit", ctypes.c_int,
      [ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_scene), ctypes.POINTER(crsh_hits), P, ctypes.c_size_t, P]),
+    ("crsh_closest_hit_timed", ctypes.c_int,
+     [ctypes.POINTER(crsh_hierarchy), ctypes.POINTER(crsh_rays), P, ctypes.POINTER(crsh_scene),
+      ctypes.POINTER(crsh_pairs), ctypes.POINTER(crsh_hits), P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_float),
+      P]),
 ]
 
 
@@ -257,6 +261,18 @@ def crsh_closest_hit(h: crsh_hierarchy, rays: crsh_rays, n_rays: int, scene: crs
     _check("crsh_closest_hit", load().crsh_closest_hit(ctypes.byref(h), ctypes.byref(rays), P(n_rays),
                                                        ctypes.byref(scene), ctypes.byref(pairs), ctypes.byref(out),
                                                        P(counters), P(workspace), workspace_bytes, P(stream)))
+
+
+def crsh_closest_hit_timed(h: crsh_hierarchy, rays: crsh_rays, n_rays: int, scene: crsh_scene, pairs: crsh_pairs,
+                           out: crsh_hits, counters: int, workspace: int, workspace_bytes: int, stream: int) -> float:
+    """crsh_closest_hit that also returns its final-test kernel's duration in ms (synchronous;
+    measurement only)."""
+    ms = ctypes.c_float(0.0)
+    _check("crsh_closest_hit_timed",
+           load().crsh_closest_hit_timed(ctypes.byref(h), ctypes.byref(rays), P(n_rays), ctypes.byref(scene),
+                                         ctypes.byref(pairs), ctypes.byref(out), P(counters), P(workspace),
+                                         workspace_bytes, ctypes.byref(ms), P(stream)))
+    return float(ms.value)
 
 
 def crsh_bruteforce_closest_hit(rays: crsh_rays, n_rays: int, scene: crsh_scene, out: crsh_hits, workspace: int,

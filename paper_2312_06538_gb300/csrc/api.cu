@@ -253,6 +253,33 @@ crsh_status crsh_closest_hit(const crsh_hierarchy* h, const crsh_rays* rays, con
                               static_cast<cudaStream_t>(stream), dev);
 }
 
+crsh_status crsh_closest_hit_timed(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
+                                   const crsh_scene* scene, const crsh_pairs* pairs, crsh_hits* out,
+                                   crsh_counters* counters, void* workspace, size_t workspace_bytes,
+                                   float* kernel_ms, void* stream) {
+    if (!hier_ok(h) || !rays_ok(rays) || !n_rays || !scene_ok(scene, true) || !pairs || !pairs->node ||
+        !pairs->tri || !pairs->count || !out || !out->tri || !out->t || !out->u || !out->v || !counters ||
+        !ws_ok(workspace) || !kernel_ms)
+        return CRSH_ERR_INVALID_ARG;
+    if (!words_ok(pairs->words, h)) return CRSH_ERR_INVALID_ARG;
+    DeviceInfo dev;
+    if (!current_device(dev)) return CRSH_ERR_CUDA;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess) return CRSH_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return CRSH_ERR_CUDA;
+    }
+    crsh_status st = closest_hit_launch(h, rays, n_rays, scene, pairs, out, counters, workspace, workspace_bytes, s,
+                                        dev, e0, e1);
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = CRSH_ERR_CUDA;
+    if (st == CRSH_OK && cudaEventElapsedTime(kernel_ms, e0, e1) != cudaSuccess) st = CRSH_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 crsh_status crsh_closest_hit_noalloc(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
                                      const crsh_scene* scene, const crsh_pairs* pairs, crsh_hits* out,
                                      crsh_counters* counters, void* stream) {

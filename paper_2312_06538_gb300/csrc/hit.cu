@@ -786,7 +786,8 @@ static void launch_closest(const crsh_pairs* pairs, const RaysDev& rd, const uin
 
 crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
                                const crsh_scene* sc, const crsh_pairs* pairs, crsh_hits* out, crsh_counters* ctr,
-                               void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev) {
+                               void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev,
+                               cudaEvent_t ev_begin, cudaEvent_t ev_end) {
     if (ws_bytes < closest_hit_workspace(rays->capacity)) return CRSH_ERR_INVALID_ARG;
     unsigned long long* best = reinterpret_cast<unsigned long long*>(ws);
     unsigned* work = reinterpret_cast<unsigned*>(best + rays->capacity);   // in the 256 spare bytes
@@ -795,6 +796,7 @@ crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, c
     launch_pdl(k_fill_best, fb, 256, 0, s, best, n_rays, cap, work, ctr);
     const RaysDev rd = rays_dev(rays);
     const float4* mt = reinterpret_cast<const float4*>(sc->tri_mt);
+    if (ev_begin && cudaEventRecord(ev_begin, s) != cudaSuccess) return CRSH_ERR_CUDA;
     switch (h->bundle) {
         case 2: launch_closest<2>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
         case 4: launch_closest<4>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
@@ -804,6 +806,7 @@ crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, c
         case 64: launch_closest<64>(pairs, rd, n_rays, cap, mt, best, work, ctr, s, dev); break;
         default: return CRSH_ERR_INVALID_ARG;
     }
+    if (ev_end && cudaEventRecord(ev_end, s) != cudaSuccess) return CRSH_ERR_CUDA;
     launch_pdl(k_finalize, fb, 256, 0, s, rd, n_rays, cap, *sc, best, *out);
     return cudaPeekAtLastError() == cudaSuccess ? CRSH_OK : CRSH_ERR_CUDA;
 }

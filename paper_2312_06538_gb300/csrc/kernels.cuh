@@ -91,9 +91,11 @@ crsh_status traverse_launch(const crsh_hierarchy* h, const crsh_scene* sc, const
                             const DeviceInfo& dev);
 
 size_t closest_hit_workspace(uint32_t ray_capacity);
+// ev_begin / ev_end (optional): events recorded on s around the final-test kernel (measurement).
 crsh_status closest_hit_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
                                const crsh_scene* sc, const crsh_pairs* pairs, crsh_hits* out, crsh_counters* ctr,
-                               void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev);
+                               void* ws, size_t ws_bytes, cudaStream_t s, const DeviceInfo& dev,
+                               cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 crsh_status closest_hit_noalloc_launch(const crsh_hierarchy* h, const crsh_rays* rays, const uint32_t* n_rays,
                                        const crsh_scene* sc, const crsh_pairs* pairs, crsh_hits* out,
                                        crsh_counters* ctr, cudaStream_t s, const DeviceInfo& dev);

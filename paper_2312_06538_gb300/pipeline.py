@@ -175,6 +175,12 @@ class Pipeline:
                            self.hits if hits is None else hits, _ptr(self.counters), _ptr(self.ws_hit),
                            self.ws_hit_bytes, stream)
 
+    def closest_hit_timed(self, stream: int) -> float:
+        """closest_hit() that returns the final-test kernel's own duration in ms (synchronous;
+        crsh_closest_hit_timed, measurement only)."""
+        return C.crsh_closest_hit_timed(self.hier, self.rays, _ptr(self.n_rays), self.scene, self.pairs, self.hits,
+                                        _ptr(self.counters), _ptr(self.ws_hit), self.ws_hit_bytes, stream)
+
     def bruteforce(self, stream: Optional[int] = None):
         stream = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
         C.crsh_bruteforce_closest_hit(self.rays, _ptr(self.n_rays), self.scene, self.hits, _ptr(self.ws_hit),

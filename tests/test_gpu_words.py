@@ -82,3 +82,19 @@ def test_words_full_size_config3_against_oracle_sample():
     rep = parity.compare_hits(got, oracle.bruteforce(sub, w.scene.verts), sub, w.scene.verts)
     parity.check_report(rep, label="config 3, word form, 800 sampled rays")
     assert rep["hits"] > 100
+
+
+def test_timed_closest_hit_matches_the_plain_call():
+    """crsh_closest_hit_timed (the bench's kernel timing) gives the plain call's hits and counters bit
+    for bit, in both forms of level 1, and a positive kernel time."""
+    w = synthetic.make(2, res=96)
+    for p, c in _both(w):
+        s = torch.cuda.current_stream().cuda_stream
+        ref = [np.array(x, copy=True) for x in p.hits_host()]
+        ms = p.closest_hit_timed(s)
+        assert ms > 0.0
+        for x, y in zip(ref, p.hits_host()):
+            assert np.array_equal(np.asarray(x).view(np.uint32), np.asarray(y).view(np.uint32))
+        c2 = p.read_counters()
+        for k in ("final_tests", "final_hits", "final_tests_paper", "status"):
+            assert c2[k] == c[k], (k, c2[k], c[k])
