@@ -297,7 +297,10 @@ const char *crsh_status_string(crsh_status s);
 /* Triangle bounding spheres (centroid centre, largest vertex distance, padded
  * outward for FP32 rounding) and the per-triangle record of the final tests
  * (v0, edges v1 - v0 and v2 - v0, normal, and the bounding sphere the final
- * tests check a ray's line against before Moller-Trumbore).  Writes
+ * tests check a ray's line against before Moller-Trumbore: the tightest of
+ * the spheres about the centroid, the three edge midpoints and the
+ * circumcentre that hold the triangle, padded like the triangle spheres; the
+ * traversal keeps the centroid spheres).  Writes
  * scene->tri_sphere and scene->tri_mt. */
 crsh_status crsh_prepare_scene(const crsh_scene *scene, void *stream);
 
